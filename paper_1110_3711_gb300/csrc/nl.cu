@@ -1,0 +1,557 @@
+// NL stage (Sections 2 and 4.1 of the paper): cell-linked list on the GPU.
+//
+//   k_hash        cell of every particle: c_d = floor((x_d - min_d) / s), linear
+//                 id cx + nx (cy + ny cz) (cells follow X, Y, Z; Section 4.4);
+//                 keys and source positions are scattered to persistent-id
+//                 order, so that the stable sort below yields the (cell, id)
+//                 order no matter how the particles were ordered before.
+//   radix sort    stable LSD, 8-bit digits: k_radix_hist (tile histograms),
+//                 exclusive scan (digit-major), k_radix_scatter (ranks from
+//                 warp match + per-warp digit counters, no atomics, stable).
+//   k_reorder     gather of every fluid array into the sorted order, plus the
+//                 packed PI inputs of Section 4.3 {pos, P/rho^2}, {vel, rho}
+//                 and the largest sound speed (Section 4.1 maxima).
+//   cell starts   exclusive scan of the per-cell counts: start[c] = number of
+//                 particles in cells below c, i.e. CellBeginEnd of Fig. 8 with
+//                 empty cells as equal begin and end.
+// All kernels are HBM-bound; grids are sized from the particle count.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+// ------------------------------------------------------------------ cells --
+
+// floor((x - mn) / s) with IEEE division, computed through the reciprocal and
+// corrected by a true division when the quotient is within 1e-9 of an integer
+// (the only case where the two can round to different sides).
+__device__ __forceinline__ int axis_cell(double x, double mn, double s, double inv_s, int n)
+{
+    double d = x - mn;
+    double t = d * inv_s;
+    double f = floor(t);
+    if (t - f < 1e-9 || (f + 1.0) - t < 1e-9) f = floor(__ddiv_rn(d, s));
+    if (!(f >= 0.0) || f >= (double)n) return -1;
+    return (int)f;
+}
+
+__device__ __forceinline__ uint32_t cell_of(const DevParams &P, double x, double y, double z)
+{
+    int cx = axis_cell(x, P.dom_min[0], P.s, P.inv_s, P.nx);
+    int cy = axis_cell(y, P.dom_min[1], P.s, P.inv_s, P.ny);
+    int cz = axis_cell(z, P.dom_min[2], P.s, P.inv_s, P.nz);
+    if (cx < 0 || cy < 0 || cz < 0) return P.ncells;
+    return (uint32_t)cx + (uint32_t)P.nx * ((uint32_t)cy + (uint32_t)P.ny * (uint32_t)cz);
+}
+
+// One thread per particle (current order i).  key_by_id[id - id_base] = cell,
+// val_by_id[id - id_base] = i; count[cell] += 1.
+__global__ void k_hash(const double *__restrict__ x, const double *__restrict__ y,
+                       const double *__restrict__ z, const uint32_t *__restrict__ id,
+                       uint32_t id_base, int n, DevParams P, uint32_t *__restrict__ key_by_id,
+                       uint32_t *__restrict__ val_by_id, uint32_t *__restrict__ count,
+                       Scalars *sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    uint32_t c = cell_of(P, x[i], y[i], z[i]);
+    uint32_t k = id ? id[i] - id_base : (uint32_t)i;
+    key_by_id[k] = c;
+    val_by_id[k] = (uint32_t)i;
+    atomicAdd(&count[c], 1u);
+    if (c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
+}
+
+// ------------------------------------------------------------- radix sort --
+
+constexpr int RS_THREADS = 256;
+constexpr int RS_WARPS = RS_THREADS / 32;
+constexpr int RS_IPT = 8;
+constexpr int RS_TILE = RS_THREADS * RS_IPT;
+
+int radix_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
+
+__global__ void __launch_bounds__(RS_THREADS)
+k_radix_hist(const uint32_t *__restrict__ keys, int n, int shift, int tiles,
+             uint32_t *__restrict__ hist)
+{
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    int base = blockIdx.x * RS_TILE;
+#pragma unroll
+    for (int k = 0; k < RS_IPT; ++k) {
+        int idx = base + k * RS_THREADS + threadIdx.x;
+        if (idx < n) atomicAdd(&h[(keys[idx] >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    hist[threadIdx.x * tiles + blockIdx.x] = h[threadIdx.x];
+}
+
+// Stable scatter of one tile.  Warp w owns elements [w*256, (w+1)*256) of the
+// tile, visited as 8 rounds of 32 consecutive elements, so (warp, round, lane)
+// is the element order; an element's rank is the count of equal digits before
+// it: earlier warps (prefix of the per-warp counters), earlier rounds of its
+// warp (the counter before this round) and lower lanes of its round (match).
+__global__ void __launch_bounds__(RS_THREADS)
+k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t *__restrict__ vin,
+                uint32_t *__restrict__ kout, uint32_t *__restrict__ vout, int n, int shift,
+                int tiles, const uint32_t *__restrict__ off)
+{
+    __shared__ uint32_t whist[RS_WARPS][256];
+    __shared__ uint32_t goff[256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int t = threadIdx.x; t < RS_WARPS * 256; t += RS_THREADS) (&whist[0][0])[t] = 0;
+    goff[threadIdx.x] = off[threadIdx.x * tiles + blockIdx.x];
+    __syncthreads();
+    const unsigned lt = (1u << lane) - 1u;
+    const int base = blockIdx.x * RS_TILE + warp * (RS_IPT * 32);
+    uint32_t key[RS_IPT], val[RS_IPT], rank[RS_IPT];
+#pragma unroll
+    for (int k = 0; k < RS_IPT; ++k) {
+        int idx = base + k * 32 + lane;
+        bool valid = idx < n;
+        key[k] = valid ? kin[idx] : 0u;
+        val[k] = valid ? vin[idx] : 0u;
+        uint32_t d = valid ? ((key[k] >> shift) & 255u) : 256u;
+        unsigned peers = __match_any_sync(0xffffffffu, d);
+        uint32_t before = valid ? whist[warp][d] : 0u;
+        rank[k] = before + __popc(peers & lt);
+        __syncwarp();
+        if (valid && lane == __ffs(peers) - 1) whist[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    {
+        uint32_t sum = 0;
+        const int d = threadIdx.x;  // RS_THREADS == 256 digits
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) {
+            uint32_t t = whist[w][d];
+            whist[w][d] = sum;
+            sum += t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < RS_IPT; ++k) {
+        int idx = base + k * 32 + lane;
+        if (idx < n) {
+            uint32_t d = (key[k] >> shift) & 255u;
+            uint32_t pos = goff[d] + whist[warp][d] + rank[k];
+            kout[pos] = key[k];
+            vout[pos] = val[k];
+        }
+    }
+}
+
+// ------------------------------------------------------------------- scan --
+
+// exclusive scan of one block's tile; returns the tile total to thread 0
+__device__ __forceinline__ uint32_t block_exclusive(uint32_t v, uint32_t *smem)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += t;
+    }
+    if (lane == 31) smem[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int nw = blockDim.x >> 5;
+        uint32_t s = lane < nw ? smem[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t t = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += t;
+        }
+        if (lane < nw) smem[lane] = s;  // inclusive per warp
+    }
+    __syncthreads();
+    uint32_t warp_prefix = warp ? smem[warp - 1] : 0u;
+    uint32_t total = smem[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    smem[32] = total;
+    return warp_prefix + x - v;
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_reduce(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t red[32];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k)
+        if (base + k < n) s += in[base + k];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        uint32_t t = red[threadIdx.x];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (threadIdx.x == 0) part[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of the partials in place
+__global__ void __launch_bounds__(kScanBlock) k_scan_partials(uint32_t *part, int64_t np)
+{
+    __shared__ uint32_t smem[33];
+    uint32_t carry = 0;
+    for (int64_t b = 0; b < np; b += kScanBlock) {
+        int64_t i = b + threadIdx.x;
+        uint32_t v = i < np ? part[i] : 0u;
+        uint32_t ex = block_exclusive(v, smem);
+        __syncthreads();
+        uint32_t tot = smem[32];
+        if (i < np) part[i] = carry + ex;
+        carry += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_down(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *__restrict__ part)
+{
+    __shared__ uint32_t smem[33];
+    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = base + k < n ? in[base + k] : 0u;
+        s += v[k];
+    }
+    uint32_t ex = block_exclusive(s, smem) + part[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (base + k < n) out[base + k] = ex;
+        ex += v[k];
+    }
+}
+
+size_t scan_partials(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
+
+int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                       uint32_t *partials, cudaStream_t st)
+{
+    if (n <= 0) return SPH_OK;
+    int64_t blocks = (n + kScanTile - 1) / kScanTile;
+    SPH_LAUNCH(ctx, k_scan_reduce, (unsigned)blocks, kScanBlock, 0, st, in, n, partials);
+    SPH_LAUNCH(ctx, k_scan_partials, 1, kScanBlock, 0, st, partials, blocks);
+    SPH_LAUNCH(ctx, k_scan_down, (unsigned)blocks, kScanBlock, 0, st, in, out, n, partials);
+    return check_cuda(cudaGetLastError());
+}
+
+// Sort (key, val) pairs of length n with `passes` 8-bit passes; the result is
+// in (kout, vout).  tmp buffers have length n.
+static int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t *ktmp,
+                      uint32_t *vtmp, uint32_t *kout, uint32_t *vout, int n, int passes,
+                      cudaStream_t st)
+{
+    if (n <= 0) return SPH_OK;
+    Workspace &w = ctx->w;
+    int tiles = radix_tiles(n);
+    // ping-pong so that the last pass lands in (kout, vout)
+    const uint32_t *ks = kin, *vs = vin;
+    for (int p = 0; p < passes; ++p) {
+        bool last = p == passes - 1;
+        bool to_out = ((passes - 1 - p) % 2) == 0;
+        uint32_t *kd = to_out ? kout : ktmp;
+        uint32_t *vd = to_out ? vout : vtmp;
+        (void)last;
+        int shift = 8 * p;
+        SPH_LAUNCH(ctx, k_radix_hist, tiles, RS_THREADS, 0, st, ks, n, shift, tiles, w.radix_hist);
+        int rc = exclusive_scan_u32(ctx, w.radix_hist, w.radix_hist, (int64_t)256 * tiles,
+                                    w.scan_part, st);
+        if (rc) return rc;
+        SPH_LAUNCH(ctx, k_radix_scatter, tiles, RS_THREADS, 0, st, ks, vs, kd, vd, n, shift,
+                   tiles, w.radix_hist);
+        ks = kd;
+        vs = vd;
+    }
+    return check_cuda(cudaGetLastError());
+}
+
+// ---------------------------------------------------------------- reorder --
+
+template <typename Real> struct Vec4;
+template <> struct Vec4<float> { typedef float4 T; };
+template <> struct Vec4<double> { typedef double4_32a T; };
+
+// Tait pressure over rho^2 and sound speed, float64 form.
+__device__ __forceinline__ void eos64(const DevParams &P, double rho, double *pr, double *c)
+{
+    double r = rho * P.inv_rho0;
+    double pw, cs;
+    if (P.gamma_is_7) {
+        double r2 = r * r;
+        double r3 = r2 * r;
+        pw = r3 * r3 * r;
+        cs = r3;
+    } else {
+        pw = pow(r, P.gamma);
+        cs = pow(r, 0.5 * (P.gamma - 1.0));
+    }
+    *pr = P.B * (pw - 1.0) / (rho * rho);
+    *c = P.c0 * cs;
+}
+
+// Tait pressure over rho^2 and sound speed, float32 form: with delta = rho/rho0
+// - 1 (small), (1 + delta)^7 - 1 is evaluated by its binomial expansion to
+// avoid the cancellation of pow(...) - 1 in float32.
+__device__ __forceinline__ void eos32(const DevParams &P, float rho, float *pr, float *c)
+{
+    float d = (rho - (float)P.rho0) * P.inv_rho0f;
+    float pw1, cs;
+    if (P.gamma_is_7) {
+        pw1 = d * fmaf(d, fmaf(d, fmaf(d, fmaf(d, fmaf(d, d + 7.0f, 21.0f), 35.0f), 35.0f), 21.0f), 7.0f);
+        float r = 1.0f + d;
+        cs = r * r * r;
+    } else {
+        float l = log1pf(d);
+        pw1 = expm1f((float)P.gamma * l);
+        cs = expf(0.5f * ((float)P.gamma - 1.0f) * l);
+    }
+    *pr = P.Bf * pw1 / (rho * rho);
+    *c = P.c0f * cs;
+}
+
+__device__ __forceinline__ void cell_origin(const DevParams &P, uint32_t c, double *ox, double *oy,
+                                            double *oz)
+{
+    uint32_t cx = c % (uint32_t)P.nx;
+    uint32_t t = c / (uint32_t)P.nx;
+    uint32_t cy = t % (uint32_t)P.ny;
+    uint32_t cz = t / (uint32_t)P.ny;
+    *ox = P.dom_min[0] + (double)cx * P.s;
+    *oy = P.dom_min[1] + (double)cy * P.s;
+    *oz = P.dom_min[2] + (double)cz * P.s;
+}
+
+// Threads [0, nf): gather fluid arrays from buffer `src` to buffer `dst` in the
+// sorted order and write the packed PI inputs.  Threads [nf, nf+nb): refresh
+// the packed pressure/density of boundary particle (i - nf).  Block max of the
+// sound speed goes to sc->mx.c.
+template <typename Real, bool SPLIT>
+__global__ void __launch_bounds__(256)
+k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
+          const uint32_t *__restrict__ val_sorted,
+          const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
+          const Real *__restrict__ svx, const Real *__restrict__ svy, const Real *__restrict__ svz,
+          const Real *__restrict__ svmx, const Real *__restrict__ svmy, const Real *__restrict__ svmz,
+          const Real *__restrict__ srho, const Real *__restrict__ srhom, const uint32_t *__restrict__ sid,
+          double *__restrict__ dx, double *__restrict__ dy, double *__restrict__ dz,
+          Real *__restrict__ dvx, Real *__restrict__ dvy, Real *__restrict__ dvz,
+          Real *__restrict__ dvmx, Real *__restrict__ dvmy, Real *__restrict__ dvmz,
+          Real *__restrict__ drho, Real *__restrict__ drhom, uint32_t *__restrict__ did,
+          typename Vec4<Real>::T *__restrict__ posp, typename Vec4<Real>::T *__restrict__ velr,
+          uint32_t *__restrict__ cell, const Real *__restrict__ brho,
+          typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
+          const int32_t *__restrict__ bstart, Scalars *sc)
+{
+    __shared__ double red[32];
+    typedef typename Vec4<Real>::T V4;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double cmax = 0.0;
+    if (i < nf) {
+        uint32_t s = val_sorted[i];
+        uint32_t c = key_sorted[i];
+        double x = sx[s], y = sy[s], z = sz[s];
+        Real vx = svx[s], vy = svy[s], vz = svz[s];
+        Real rho = srho[s];
+        dx[i] = x; dy[i] = y; dz[i] = z;
+        dvx[i] = vx; dvy[i] = vy; dvz[i] = vz;
+        dvmx[i] = svmx[s]; dvmy[i] = svmy[s]; dvmz[i] = svmz[s];
+        drho[i] = rho; drhom[i] = srhom[s];
+        did[i] = sid[s];
+        cell[i] = c;
+        V4 pp, vv;
+        if (SPLIT) {
+            float pr, cs;
+            eos32(P, (float)rho, &pr, &cs);
+            double ox = 0.0, oy = 0.0, oz = 0.0;
+            if (c < P.ncells) cell_origin(P, c, &ox, &oy, &oz);
+            pp.x = (Real)(x - ox); pp.y = (Real)(y - oy); pp.z = (Real)(z - oz); pp.w = (Real)pr;
+            if (c < P.ncells) cmax = (double)cs;
+        } else {
+            double pr, cs;
+            eos64(P, (double)rho, &pr, &cs);
+            pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z; pp.w = (Real)pr;
+            if (c < P.ncells) cmax = cs;
+        }
+        vv.x = vx; vv.y = vy; vv.z = vz; vv.w = rho;
+        posp[i] = pp;
+        velr[i] = vv;
+    } else if (i < nf + nb) {
+        int j = i - nf;
+        if (j < bstart[P.ncells]) {
+            Real rho = brho[j];
+            V4 pp = bposp[j];
+            V4 vv;
+            vv.x = 0; vv.y = 0; vv.z = 0; vv.w = rho;
+            if (SPLIT) {
+                float pr, cs;
+                eos32(P, (float)rho, &pr, &cs);
+                pp.w = (Real)pr;
+                cmax = (double)cs;
+            } else {
+                double pr, cs;
+                eos64(P, (double)rho, &pr, &cs);
+                pp.w = (Real)pr;
+                cmax = cs;
+            }
+            bposp[j] = pp;
+            bvelr[j] = vv;
+        }
+    }
+    block_max_to(&sc->mx.c, cmax, red);
+}
+
+// Boundary list (built once): gather the id-ordered boundary state staged in
+// `in_*` into sorted order, with packed positions.
+template <typename Real, bool SPLIT>
+__global__ void k_boundary_place(int nb, uint32_t nf, DevParams P,
+                                 const uint32_t *__restrict__ key_sorted,
+                                 const uint32_t *__restrict__ val_sorted,
+                                 const double *__restrict__ in_pos, const double *__restrict__ in_rho,
+                                 const double *__restrict__ in_rhom,
+                                 double *bx, double *by, double *bz, Real *brho, Real *brhom,
+                                 uint32_t *bid, uint32_t *bcell,
+                                 typename Vec4<Real>::T *bposp, typename Vec4<Real>::T *bvelr)
+{
+    typedef typename Vec4<Real>::T V4;
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    uint32_t k = val_sorted[i];
+    uint32_t c = key_sorted[i];
+    double x = in_pos[3 * (size_t)(nf + k)], y = in_pos[3 * (size_t)(nf + k) + 1],
+           z = in_pos[3 * (size_t)(nf + k) + 2];
+    bx[i] = x; by[i] = y; bz[i] = z;
+    brho[i] = (Real)in_rho[nf + k];
+    brhom[i] = (Real)in_rhom[nf + k];
+    bid[i] = nf + k;
+    bcell[i] = c;
+    V4 pp, vv;
+    if (SPLIT) {
+        double ox = 0.0, oy = 0.0, oz = 0.0;
+        if (c < P.ncells) cell_origin(P, c, &ox, &oy, &oz);
+        pp.x = (Real)(x - ox); pp.y = (Real)(y - oy); pp.z = (Real)(z - oz);
+    } else {
+        pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z;
+    }
+    pp.w = 0;
+    vv.x = 0; vv.y = 0; vv.z = 0; vv.w = (Real)in_rho[nf + k];
+    bposp[i] = pp;
+    bvelr[i] = vv;
+}
+
+__global__ void k_boundary_hash(const double *__restrict__ pos, uint32_t nf, int nb, DevParams P,
+                                uint32_t *key_by_id, uint32_t *val_by_id, uint32_t *count)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nb) return;
+    size_t g = (size_t)(nf + k);
+    uint32_t c = cell_of(P, pos[3 * g], pos[3 * g + 1], pos[3 * g + 2]);
+    key_by_id[k] = c;
+    val_by_id[k] = (uint32_t)k;
+    atomicAdd(&count[c], 1u);
+}
+
+static int key_passes(uint32_t ncells)
+{
+    int bits = 0;
+    while (bits < 32 && ((uint64_t)1 << bits) <= (uint64_t)ncells) ++bits;
+    return bits <= 8 ? 1 : (bits + 7) / 8;
+}
+
+// ------------------------------------------------------------ entry points --
+
+template <typename Real, bool SPLIT>
+static int nl_fluid_t(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int nf = (int)ctx->nf, nb = (int)ctx->nb;
+    int src = ctx->cur, dst = 1 - ctx->cur;
+    const int T = 256;
+    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2), st)))
+        return SPH_ERR_CUDA;
+    if (nf > 0) {
+        SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src],
+                   w.id[src], 0u, nf, ctx->dp, w.key_by_id, w.val_by_id, w.count, w.sc);
+        int rc = radix_sort(ctx, w.key_by_id, w.val_by_id, w.key_tmp, w.val_tmp, w.key_sorted,
+                            w.val_sorted, nf, ctx->nl_passes, st);
+        if (rc) return rc;
+    }
+    int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.fstart, (int64_t)ctx->ncells + 2,
+                                w.scan_part, st);
+    if (rc) return rc;
+    int tot = nf + nb;
+    if (tot > 0) {
+        SPH_LAUNCH(ctx, (k_reorder<Real, SPLIT>), (tot + T - 1) / T, T, 0, st, nf, nb, ctx->dp,
+                   w.key_sorted, w.val_sorted, w.x[src], w.y[src], w.z[src], (const Real *)w.vx[src],
+                   (const Real *)w.vy[src], (const Real *)w.vz[src], (const Real *)w.vmx[src],
+                   (const Real *)w.vmy[src], (const Real *)w.vmz[src], (const Real *)w.rho[src],
+                   (const Real *)w.rhom[src], w.id[src], w.x[dst], w.y[dst], w.z[dst],
+                   (Real *)w.vx[dst], (Real *)w.vy[dst], (Real *)w.vz[dst], (Real *)w.vmx[dst],
+                   (Real *)w.vmy[dst], (Real *)w.vmz[dst], (Real *)w.rho[dst], (Real *)w.rhom[dst],
+                   w.id[dst], (typename Vec4<Real>::T *)w.posp, (typename Vec4<Real>::T *)w.velr,
+                   w.cell, (const Real *)w.brho, (typename Vec4<Real>::T *)w.bposp,
+                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.sc);
+    }
+    ctx->cur = dst;
+    return check_cuda(cudaGetLastError());
+}
+
+int nl_fluid(sph_ctx *ctx)
+{
+    if (ctx->precision == SPH_FP32_SPLIT) return nl_fluid_t<float, true>(ctx);
+    return nl_fluid_t<double, false>(ctx);
+}
+
+// Build the boundary list from the id-ordered state staged in w.stage
+// (pos 3N | vel 3N | rho N | velm 3N | rhom N).
+template <typename Real, bool SPLIT>
+static int nl_boundary_t(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int nf = (int)ctx->nf, nb = (int)ctx->nb;
+    size_t N = (size_t)(nf + nb);
+    const double *in_pos = w.stage;
+    const double *in_rho = w.stage + 6 * N;
+    const double *in_rhom = w.stage + 10 * N;
+    const int T = 256;
+    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2), st)))
+        return SPH_ERR_CUDA;
+    if (nb > 0) {
+        SPH_LAUNCH(ctx, k_boundary_hash, (nb + T - 1) / T, T, 0, st, in_pos, (uint32_t)nf, nb,
+                   ctx->dp, w.key_by_id, w.val_by_id, w.count);
+        int rc = radix_sort(ctx, w.key_by_id, w.val_by_id, w.key_tmp, w.val_tmp, w.key_sorted,
+                            w.val_sorted, nb, ctx->nl_passes, st);
+        if (rc) return rc;
+        SPH_LAUNCH(ctx, (k_boundary_place<Real, SPLIT>), (nb + T - 1) / T, T, 0, st, nb,
+                   (uint32_t)nf, ctx->dp, w.key_sorted, w.val_sorted, in_pos, in_rho, in_rhom,
+                   w.bx, w.by, w.bz, (Real *)w.brho, (Real *)w.brhom, w.bid, w.bcell,
+                   (typename Vec4<Real>::T *)w.bposp, (typename Vec4<Real>::T *)w.bvelr);
+    }
+    int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.bstart, (int64_t)ctx->ncells + 2,
+                                w.scan_part, st);
+    if (rc) return rc;
+    return check_cuda(cudaGetLastError());
+}
+
+int nl_boundary_build(sph_ctx *ctx)
+{
+    ctx->nl_passes = key_passes(ctx->ncells);
+    if (ctx->precision == SPH_FP32_SPLIT) return nl_boundary_t<float, true>(ctx);
+    return nl_boundary_t<double, false>(ctx);
+}
+
+}  // namespace sph

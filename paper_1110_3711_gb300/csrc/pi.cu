@@ -1,0 +1,402 @@
+// PI stage (Sections 2, 4.3-4.5 of the paper): particle interactions.
+//
+// One thread per target particle (Section 4): its own data stay in registers
+// and its sums are written once at the end (Section 4.5).  Fluid targets
+// evaluate F-F and F-B in one kernel (Section 4.5, optimisation E); boundary
+// targets have their own B-F kernel (continuity only).  Candidates are the
+// particles of the 27 surrounding cells, visited as the 9 x-runs of Fig. 10 /
+// Fig. 11 (cells x-1, x, x+1 of one (y, z) row are contiguous after NL).
+//
+// Per ordered pair a <- b with r_ab = x_a - x_b, r = |r_ab| < 2h, q = r/h:
+//   grad_a W_ab = F r_ab,  F = aD/h^2 (-3 + 2.25 q)         (q < 1)
+//                            = -0.75 aD/h (2 - q)^2 / r       (1 <= q < 2), aD = 1/(pi h^3)
+//   mu = h v_ab.r_ab / (r^2 + eta^2);  Pi = -alpha (c_a + c_b) mu / (rho_a + rho_b) if v_ab.r_ab < 0
+//   ace_a += -m (P_a/rho_a^2 + P_b/rho_b^2 + Pi) F r_ab      (fluid targets)
+//   ar_a  +=  m F v_ab.r_ab
+//   visc   = max(visc, |mu|)
+// then ace_a += g; the block maxima of |ace|^2 and visc feed the time step.
+//
+// SPH_FP64: absolute float64 positions, every operation in float64.
+// SPH_FP32_SPLIT: float32 positions relative to the origin of the particle's
+// cell; a candidate in the neighbouring cell (dx, dy, dz) is shifted by
+// (dx, dy, dz) * s, so all differences stay small and float32-accurate.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ void cell_xyz(const DevParams &P, uint32_t c, int *cx, int *cy, int *cz)
+{
+    uint32_t t = c / (uint32_t)P.nx;
+    *cx = (int)(c - t * (uint32_t)P.nx);
+    *cy = (int)(t % (uint32_t)P.ny);
+    *cz = (int)(t / (uint32_t)P.ny);
+}
+
+// ------------------------------------------------------------------ FP64 --
+
+struct Acc64 {
+    double ax, ay, az, ar, vis;
+};
+
+template <bool MOMENTUM>
+__device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa, const double4_32a &va,
+                                       double ca, const double4_32a &pb, const double4_32a &vb, double rx,
+                                       double ry, double rz, double r2, Acc64 &o)
+{
+    double rinv = rsqrt(r2);
+    double r = r2 * rinv;
+    double q = r * P.invh;
+    double F = q < 1.0 ? P.kA64 * (-3.0 + 2.25 * q) : P.kB64 * (2.0 - q) * (2.0 - q) * rinv;
+    double dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
+    double vdr = dvx * rx + dvy * ry + dvz * rz;
+    double mu = P.h * vdr / (r2 + P.eta2);
+    if (MOMENTUM) {
+        double Pi = 0.0;
+        if (vdr < 0.0) {
+            double rb = vb.w * P.inv_rho0;
+            double cb = P.gamma_is_7 ? P.c0 * rb * rb * rb : P.c0 * pow(rb, 0.5 * (P.gamma - 1.0));
+            Pi = -P.alpha * (ca + cb) * mu / (va.w + vb.w);
+        }
+        double coef = -(pa.w + pb.w + Pi) * F;
+        o.ax += coef * rx;
+        o.ay += coef * ry;
+        o.az += coef * rz;
+    }
+    o.ar += vdr * F;
+    o.vis = fmax(o.vis, fabs(mu));
+}
+
+template <bool MOMENTUM>
+__device__ __forceinline__ void runs64(const DevParams &P, int self, const double4_32a &pa,
+                                       const double4_32a &va, double ca, int cx, int cy, int cz,
+                                       const double4_32a *__restrict__ posp,
+                                       const double4_32a *__restrict__ velr,
+                                       const int32_t *__restrict__ start, Acc64 &o)
+{
+    const double s2 = 4.0 * P.h * P.h;
+    int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= P.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= P.ny) continue;
+            int row = P.nx * (y + P.ny * z);
+            int j0 = start[row + x0], j1 = start[row + x1 + 1];
+            for (int j = j0; j < j1; ++j) {
+                if (j == self) continue;
+                double4_32a pb = posp[j];
+                double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+                double r2 = rx * rx + ry * ry + rz * rz;
+                if (r2 < s2) pair64<MOMENTUM>(P, pa, va, ca, pb, velr[j], rx, ry, rz, r2, o);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ double sound64(const DevParams &P, double rho)
+{
+    double r = rho * P.inv_rho0;
+    return P.gamma_is_7 ? P.c0 * r * r * r : P.c0 * pow(r, 0.5 * (P.gamma - 1.0));
+}
+
+__global__ void __launch_bounds__(128)
+k_pi_fluid64(int nf, DevParams P, const double4_32a *__restrict__ posp,
+             const double4_32a *__restrict__ velr, const uint32_t *__restrict__ cell,
+             const int32_t *__restrict__ fstart, const double4_32a *__restrict__ bposp,
+             const double4_32a *__restrict__ bvelr, const int32_t *__restrict__ bstart,
+             double4_32a *__restrict__ acc, Scalars *sc)
+{
+    __shared__ double red[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nvalid = fstart[P.ncells];
+    double f2 = 0.0, vis = 0.0;
+    if (i < nvalid) {
+        double4_32a pa = posp[i], va = velr[i];
+        int cx, cy, cz;
+        cell_xyz(P, cell[i], &cx, &cy, &cz);
+        double ca = sound64(P, va.w);
+        Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
+        runs64<true>(P, i, pa, va, ca, cx, cy, cz, posp, velr, fstart, o);
+        runs64<true>(P, -1, pa, va, ca, cx, cy, cz, bposp, bvelr, bstart, o);
+        double ax = P.mass * o.ax + P.g[0];
+        double ay = P.mass * o.ay + P.g[1];
+        double az = P.mass * o.az + P.g[2];
+        acc[i] = make_double4_32a(ax, ay, az, P.mass * o.ar);
+        f2 = __dadd_rn(__dadd_rn(__dmul_rn(ax, ax), __dmul_rn(ay, ay)), __dmul_rn(az, az));
+        vis = o.vis;
+        if (!(f2 < INFINITY) || !(o.ar == o.ar)) atomicOr(&sc->flags, SPH_FLAG_NAN);
+    } else if (i < nf) {
+        acc[i] = make_double4_32a(0.0, 0.0, 0.0, 0.0);
+    }
+    block_max_to(&sc->mx.f2, f2, red);
+    block_max_to(&sc->mx.visc, vis, red);
+}
+
+__global__ void __launch_bounds__(128)
+k_pi_boundary64(int nb, DevParams P, const double4_32a *__restrict__ bposp,
+                const double4_32a *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
+                const int32_t *__restrict__ bstart, const double4_32a *__restrict__ posp,
+                const double4_32a *__restrict__ velr, const int32_t *__restrict__ fstart,
+                double *__restrict__ bar, Scalars *sc)
+{
+    __shared__ double red[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nvalid = bstart[P.ncells];
+    double vis = 0.0;
+    if (i < nvalid) {
+        double4_32a pa = bposp[i], va = bvelr[i];
+        int cx, cy, cz;
+        cell_xyz(P, bcell[i], &cx, &cy, &cz);
+        Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
+        runs64<false>(P, -1, pa, va, 0.0, cx, cy, cz, posp, velr, fstart, o);
+        bar[i] = P.mass * o.ar;
+        vis = o.vis;
+    } else if (i < nb) {
+        bar[i] = 0.0;
+    }
+    block_max_to(&sc->mx.visc, vis, red);
+}
+
+// ------------------------------------------------------------------ FP32 --
+
+struct Acc32 {
+    float ax, ay, az, ar, vis;
+};
+
+template <bool MOMENTUM>
+__device__ __forceinline__ void pair32(const DevParams &P, const float4 &pa, const float4 &va,
+                                       float ca, const float4 &pb, const float4 &vb, float rx,
+                                       float ry, float rz, float r2, Acc32 &o)
+{
+    float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+    float r = r2 * rinv;
+    float q = r * P.invhf;
+    float t = 2.0f - q;
+    float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
+    float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
+    float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
+    float mu = __fdividef(P.hf * vdr, r2 + P.eta2f);
+    if (MOMENTUM) {
+        float rb = vb.w * P.inv_rho0f;
+        float cb = P.c0f * rb * rb * rb;
+        float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
+        float coef = -(pa.w + pb.w + Pi) * F;
+        o.ax = fmaf(coef, rx, o.ax);
+        o.ay = fmaf(coef, ry, o.ay);
+        o.az = fmaf(coef, rz, o.az);
+    }
+    o.ar = fmaf(vdr, F, o.ar);
+    o.vis = fmaxf(o.vis, fabsf(mu));
+}
+
+template <bool MOMENTUM>
+__device__ __forceinline__ void cells32(const DevParams &P, const float4 &pa, const float4 &va,
+                                        float ca, int cx, int cy, int cz,
+                                        const float4 *__restrict__ posp,
+                                        const float4 *__restrict__ velr,
+                                        const int32_t *__restrict__ start, Acc32 &o)
+{
+    for (int dz = -1; dz <= 1; ++dz) {
+        int z = cz + dz;
+        if (z < 0 || z >= P.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int y = cy + dy;
+            if (y < 0 || y >= P.ny) continue;
+            int row = P.nx * (y + P.ny * z);
+            for (int dx = -1; dx <= 1; ++dx) {
+                int x = cx + dx;
+                if (x < 0 || x >= P.nx) continue;
+                int j0 = start[row + x], j1 = start[row + x + 1];
+                // target position relative to the candidate cell's origin
+                float xa = pa.x - (float)dx * P.sf;
+                float ya = pa.y - (float)dy * P.sf;
+                float za = pa.z - (float)dz * P.sf;
+                for (int j = j0; j < j1; ++j) {
+                    float4 pb = posp[j];
+                    float rx = xa - pb.x, ry = ya - pb.y, rz = za - pb.z;
+                    float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+                    if (r2 < P.four_h2f) pair32<MOMENTUM>(P, pa, va, ca, pb, velr[j], rx, ry, rz, r2, o);
+                }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(128)
+k_pi_fluid32(int nf, DevParams P, const float4 *__restrict__ posp, const float4 *__restrict__ velr,
+             const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
+             const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
+             const int32_t *__restrict__ bstart, float4 *__restrict__ acc, Scalars *sc)
+{
+    __shared__ double red[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nvalid = fstart[P.ncells];
+    double f2 = 0.0, vis = 0.0;
+    if (i < nvalid) {
+        float4 pa = posp[i], va = velr[i];
+        int cx, cy, cz;
+        cell_xyz(P, cell[i], &cx, &cy, &cz);
+        float ra = va.w * P.inv_rho0f;
+        float ca = P.c0f * ra * ra * ra;
+        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
+        // the self pair has r_ab = 0 and v_ab = 0 and adds exactly zero
+        cells32<true>(P, pa, va, ca, cx, cy, cz, posp, velr, fstart, o);
+        cells32<true>(P, pa, va, ca, cx, cy, cz, bposp, bvelr, bstart, o);
+        float ax = fmaf(P.massf, o.ax, P.gf[0]);
+        float ay = fmaf(P.massf, o.ay, P.gf[1]);
+        float az = fmaf(P.massf, o.az, P.gf[2]);
+        acc[i] = make_float4(ax, ay, az, P.massf * o.ar);
+        f2 = (double)ax * ax + (double)ay * ay + (double)az * az;
+        vis = (double)o.vis;
+        if (!(f2 < INFINITY) || !(o.ar == o.ar)) atomicOr(&sc->flags, SPH_FLAG_NAN);
+    } else if (i < nf) {
+        acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    block_max_to(&sc->mx.f2, f2, red);
+    block_max_to(&sc->mx.visc, vis, red);
+}
+
+__global__ void __launch_bounds__(128)
+k_pi_boundary32(int nb, DevParams P, const float4 *__restrict__ bposp,
+                const float4 *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
+                const int32_t *__restrict__ bstart, const float4 *__restrict__ posp,
+                const float4 *__restrict__ velr, const int32_t *__restrict__ fstart,
+                float *__restrict__ bar, Scalars *sc)
+{
+    __shared__ double red[32];
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int nvalid = bstart[P.ncells];
+    double vis = 0.0;
+    if (i < nvalid) {
+        float4 pa = bposp[i], va = bvelr[i];
+        int cx, cy, cz;
+        cell_xyz(P, bcell[i], &cx, &cy, &cz);
+        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
+        cells32<false>(P, pa, va, 0.f, cx, cy, cz, posp, velr, fstart, o);
+        bar[i] = P.massf * o.ar;
+        vis = (double)o.vis;
+    } else if (i < nb) {
+        bar[i] = 0.f;
+    }
+    block_max_to(&sc->mx.visc, vis, red);
+}
+
+// -------------------------------------------------------- validation pass --
+
+// Exact counts in float64 with the products and sums rounded one by one (no
+// contraction), the same arithmetic as a plain CPU evaluation of
+// dx*dx + dy*dy + dz*dz < 4h^2 on absolute positions.
+__device__ __forceinline__ void count_runs(const DevParams &P, double xa, double ya, double za,
+                                           int self, int cx, int cy, int cz,
+                                           const double *__restrict__ x,
+                                           const double *__restrict__ y,
+                                           const double *__restrict__ z,
+                                           const int32_t *__restrict__ start,
+                                           unsigned long long &cand, unsigned long long &pairs)
+{
+    const double s2 = 4.0 * P.h * P.h;
+    int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
+    for (int dz = -1; dz <= 1; ++dz) {
+        int zz = cz + dz;
+        if (zz < 0 || zz >= P.nz) continue;
+        for (int dy = -1; dy <= 1; ++dy) {
+            int yy = cy + dy;
+            if (yy < 0 || yy >= P.ny) continue;
+            int row = P.nx * (yy + P.ny * zz);
+            int j0 = start[row + x0], j1 = start[row + x1 + 1];
+            for (int j = j0; j < j1; ++j) {
+                if (j == self) continue;
+                double rx = __dsub_rn(xa, x[j]), ry = __dsub_rn(ya, y[j]), rz = __dsub_rn(za, z[j]);
+                double r2 = __dadd_rn(__dadd_rn(__dmul_rn(rx, rx), __dmul_rn(ry, ry)), __dmul_rn(rz, rz));
+                cand++;
+                if (r2 < s2) pairs++;
+            }
+        }
+    }
+}
+
+__global__ void k_count_work(int nf, int nb, DevParams P, const double *__restrict__ x,
+                             const double *__restrict__ y, const double *__restrict__ z,
+                             const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
+                             const double *__restrict__ bx, const double *__restrict__ by,
+                             const double *__restrict__ bz, const uint32_t *__restrict__ bcell,
+                             const int32_t *__restrict__ bstart, unsigned long long *counts)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned long long c = 0, p = 0;
+    int cx, cy, cz;
+    if (i < nf) {
+        if (i < fstart[P.ncells]) {
+            cell_xyz(P, cell[i], &cx, &cy, &cz);
+            count_runs(P, x[i], y[i], z[i], i, cx, cy, cz, x, y, z, fstart, c, p);
+            count_runs(P, x[i], y[i], z[i], -1, cx, cy, cz, bx, by, bz, bstart, c, p);
+            atomicAdd(&counts[0], c);
+            atomicAdd(&counts[1], p);
+        }
+    } else if (i < nf + nb) {
+        int j = i - nf;
+        if (j < bstart[P.ncells]) {
+            cell_xyz(P, bcell[j], &cx, &cy, &cz);
+            count_runs(P, bx[j], by[j], bz[j], -1, cx, cy, cz, x, y, z, fstart, c, p);
+            atomicAdd(&counts[2], c);
+            atomicAdd(&counts[3], p);
+        }
+    }
+}
+
+// ------------------------------------------------------------ entry points --
+
+int pi_launch(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int nf = (int)ctx->nf, nb = (int)ctx->nb;
+    const int T = 128;
+    if (ctx->precision == SPH_FP32_SPLIT) {
+        if (nf > 0)
+            SPH_LAUNCH(ctx, k_pi_fluid32, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
+                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
+                       (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc,
+                       w.sc);
+        if (nb > 0)
+            SPH_LAUNCH(ctx, k_pi_boundary32, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
+                       (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
+                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart, (float *)w.bar,
+                       w.sc);
+    } else {
+        if (nf > 0)
+            SPH_LAUNCH(ctx, k_pi_fluid64, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
+                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
+                       (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
+                       (double4_32a *)w.acc, w.sc);
+        if (nb > 0)
+            SPH_LAUNCH(ctx, k_pi_boundary64, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
+                       (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
+                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, (double *)w.bar,
+                       w.sc);
+    }
+    return check_cuda(cudaGetLastError());
+}
+
+int count_work_launch(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int nf = (int)ctx->nf, nb = (int)ctx->nb;
+    int cur = ctx->cur;
+    if (check_cuda(cudaMemsetAsync(w.counts4, 0, 4 * sizeof(unsigned long long), st)))
+        return SPH_ERR_CUDA;
+    int tot = nf + nb;
+    if (tot == 0) return SPH_OK;
+    const int T = 128;
+    SPH_LAUNCH(ctx, k_count_work, (tot + T - 1) / T, T, 0, st, nf, nb, ctx->dp, w.x[cur], w.y[cur],
+               w.z[cur], w.cell, w.fstart, w.bx, w.by, w.bz, w.bcell, w.bstart, w.counts4);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace sph

@@ -1,0 +1,181 @@
+// Internal declarations of libsph (not part of the ABI).
+//
+// Data layout in HBM (one context):
+//   fluid state, double-buffered (NL gathers buffer `cur` into `1-cur`), SoA in
+//   sorted (cell, id) order:  x y z (f64) | vx vy vz | vmx vmy vmz | rho rhom
+//   (Real = f64 in SPH_FP64, f32 in SPH_FP32_SPLIT) | id (u32)
+//   packed PI inputs of Section 4.3: posp = {x, y, z, P/rho^2}, velr = {vx, vy,
+//   vz, rho}; in SPH_FP32_SPLIT the position is the f32 offset from the origin
+//   of the particle's cell, in SPH_FP64 it is absolute.  cell (u32) per particle.
+//   PI output acc = {ax, ay, az, drho/dt} per fluid particle.
+//   boundary state (never moves, sorted once): x y z (f64), rho rhom (Real),
+//   id (u32), packed posp/velr like the fluid, ar (Real) output.
+//   NL scratch: keys/values by id, their sorted copies, per-cell counts and
+//   first indices (fluid and boundary), radix-sort tile histograms.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/sph.h"
+
+namespace sph {
+
+// Largest value of each time-step maximum, stored as the bit pattern of a
+// non-negative double (so atomicMax on the integer is a max on the value).
+struct Maxima {
+    unsigned long long f2;    // max |f_a|^2 over fluid
+    unsigned long long c;     // max c_a over all particles in the grid
+    unsigned long long visc;  // max |h v.r / (r^2 + eta^2)| over pairs
+};
+
+struct Scalars {
+    Maxima mx;
+    double dt_last;
+    double time;
+    long long step;     // completed steps
+    uint32_t flags;
+    uint32_t pad;
+};
+
+// Constants every kernel needs, passed by value.
+struct DevParams {
+    double h, s, inv_s, rho0, inv_rho0, gamma, c0, alpha, eta2, cfl, mass, B, fixed_dt;
+    double invh, kA64, kB64;  // 1/h and the grad-W factor constants (see pi.cu)
+    double g[3];
+    double dom_min[3];
+    int nx, ny, nz;
+    uint32_t ncells;
+    int euler_every;
+    int clamp;
+    int gamma_is_7;
+    // float copies for the FP32 path
+    float hf, invhf, four_h2f, eta2f, massf, alphaf, c0f, inv_rho0f, Bf, sf;
+    float kA, kB;   // grad-W factor constants (see pi.cu)
+    float gf[3];
+};
+
+struct Workspace {
+    // fluid state
+    double *x[2], *y[2], *z[2];
+    void *vx[2], *vy[2], *vz[2], *vmx[2], *vmy[2], *vmz[2], *rho[2], *rhom[2];
+    uint32_t *id[2];
+    char *state_chunk[2];
+    size_t state_chunk_bytes;
+    // packed PI inputs / outputs (fluid)
+    void *posp, *velr, *acc;
+    uint32_t *cell;
+    // boundary
+    double *bx, *by, *bz;
+    void *brho, *brhom, *bposp, *bvelr, *bar;
+    uint32_t *bid, *bcell;
+    char *bstate_chunk;
+    size_t bstate_chunk_bytes;
+    // NL scratch
+    uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
+    uint32_t *count;          // [ncells + 2]
+    int32_t *fstart, *bstart; // [ncells + 2]
+    uint32_t *radix_hist;     // [256 * tiles]
+    uint32_t *scan_part;      // scan partials
+    // host exchange staging: 11 doubles per particle
+    double *stage;
+    Scalars *sc;
+    unsigned long long *counts4;  // validation counters
+};
+
+}  // namespace sph
+
+struct sph_ctx {
+    sph_params prm;
+    sph::DevParams dp;
+    int64_t nf, nb;
+    int dims[3];
+    uint32_t ncells;
+    int precision;
+    size_t real_size;
+    cudaStream_t stream;
+    sph::Workspace w;
+    int cur;                 // current fluid buffer
+    int nl_passes;           // radix passes of 8 bits
+    bool nl_valid, pi_valid;
+    long long launches;
+    int device;
+};
+
+namespace sph {
+
+// workspace planning (api.cu)
+size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells,
+                      Workspace *w, char *base);
+
+// NL (nl.cu)
+int nl_fluid(sph_ctx *ctx);
+int nl_boundary_build(sph_ctx *ctx);
+void nl_boundary_refresh_launch(sph_ctx *ctx, cudaStream_t st);
+int radix_tiles(int64_t n);
+size_t scan_partials(int64_t n);
+
+// PI (pi.cu)
+int pi_launch(sph_ctx *ctx);
+int count_work_launch(sph_ctx *ctx);
+
+// SU (su.cu)
+int su_launch(sph_ctx *ctx);
+
+// id-order exchange (api.cu)
+int check_cuda(cudaError_t e);
+
+// generic helpers
+constexpr int kScanBlock = 1024;
+constexpr int kScanItems = 4;
+constexpr int kScanTile = kScanBlock * kScanItems;
+
+int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                       uint32_t *partials, cudaStream_t st);
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *dst, double v)
+{
+    // non-negative doubles (and +inf / NaN, which compare above) order like
+    // their bit patterns
+    atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ float warp_maxf(float v)
+{
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide max of a non-negative value followed by one atomic per block.
+// Every thread of the block must call it.  NaN is propagated (fmax drops NaN,
+// so it is tracked separately).
+__device__ __forceinline__ void block_max_to(unsigned long long *dst, double v, double *smem32)
+{
+    bool nan = v != v;
+    unsigned anynan = __syncthreads_or(nan);
+    double m = warp_max(nan ? 0.0 : v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) smem32[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        double t = lane < nw ? smem32[lane] : 0.0;
+        t = warp_max(t);
+        if (lane == 0) atomic_max_nonneg(dst, anynan ? __longlong_as_double(0x7ff8000000000000LL) : t);
+    }
+    __syncthreads();
+}
+
+}  // namespace sph
+
+#define SPH_LAUNCH(ctx, kernel, grid, block, smem, st, ...)                       \
+    do {                                                                          \
+        kernel<<<(grid), (block), (smem), (st)>>>(__VA_ARGS__);                   \
+        (ctx)->launches++;                                                        \
+    } while (0)

@@ -1,0 +1,144 @@
+// SU stage (Section 4.1, Table 1 of the paper): time step and integration.
+//
+// The variable time step (Monaghan & Kos) uses the three maxima PI and NL left
+// in device memory:
+//   dt = CFL * min( sqrt(h / max|f|),  h / (max c + max |h v.r/(r^2+eta^2)|) )
+// computed in float64 once per block from the same bits, so every block and
+// the finaliser agree exactly.  Verlet (Table 1) with an Euler step when
+// (step + 1) % N_s == 0:
+//   v^{n+1} = v^{n-1} + 2 dt F^n  (Euler: v^n + dt F^n),  same for rho with D^n
+//   x^{n+1} = x^n + dt v^n + dt^2 F^n / 2   (always float64)
+// Boundary particles update rho only and never drop below rho0 (dynamic
+// boundaries).  k_finalize then advances time and step and clears the maxima.
+// HBM-bound: one read and one write of the state per particle.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+__device__ __forceinline__ double step_dt(const DevParams &P, const Scalars *sc)
+{
+    if (P.fixed_dt > 0.0) return P.fixed_dt;
+    double f = sqrt(__longlong_as_double((long long)sc->mx.f2));
+    double dtf = sqrt(P.h / f);
+    double dtcv = P.h / (__longlong_as_double((long long)sc->mx.c) +
+                         __longlong_as_double((long long)sc->mx.visc));
+    return P.cfl * fmin(dtf, dtcv);
+}
+
+template <typename Real> struct V4T;
+template <> struct V4T<float> { typedef float4 T; };
+template <> struct V4T<double> { typedef double4_32a T; };
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_su_fluid(int nf, DevParams P, const int32_t *__restrict__ fstart, double *__restrict__ x,
+           double *__restrict__ y, double *__restrict__ z, Real *__restrict__ vx,
+           Real *__restrict__ vy, Real *__restrict__ vz, Real *__restrict__ vmx,
+           Real *__restrict__ vmy, Real *__restrict__ vmz, Real *__restrict__ rho,
+           Real *__restrict__ rhom, const typename V4T<Real>::T *__restrict__ acc, Scalars *sc)
+{
+    __shared__ double sdt;
+    __shared__ int seuler;
+    if (threadIdx.x == 0) {
+        sdt = step_dt(P, sc);
+        seuler = ((sc->step + 1) % P.euler_every) == 0;
+    }
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf || i >= fstart[P.ncells]) return;
+    const double dt = sdt;
+    const Real dtr = (Real)dt;
+    const double hdt2 = 0.5 * dt * dt;
+    typename V4T<Real>::T f = acc[i];
+    Real v0 = vx[i], v1 = vy[i], v2 = vz[i];
+    x[i] = x[i] + dt * (double)v0 + hdt2 * (double)f.x;
+    y[i] = y[i] + dt * (double)v1 + hdt2 * (double)f.y;
+    z[i] = z[i] + dt * (double)v2 + hdt2 * (double)f.z;
+    Real r = rho[i];
+    Real nv0, nv1, nv2, nr;
+    if (seuler) {
+        nv0 = v0 + dtr * f.x;
+        nv1 = v1 + dtr * f.y;
+        nv2 = v2 + dtr * f.z;
+        nr = r + dtr * f.w;
+    } else {
+        const Real dt2 = (Real)(2.0 * dt);
+        nv0 = vmx[i] + dt2 * f.x;
+        nv1 = vmy[i] + dt2 * f.y;
+        nv2 = vmz[i] + dt2 * f.z;
+        nr = rhom[i] + dt2 * f.w;
+    }
+    vmx[i] = v0; vmy[i] = v1; vmz[i] = v2;
+    vx[i] = nv0; vy[i] = nv1; vz[i] = nv2;
+    rhom[i] = r;
+    rho[i] = nr;
+    if (!(nr == nr) || !(nv0 == nv0) || !(nv1 == nv1) || !(nv2 == nv2))
+        atomicOr(&sc->flags, SPH_FLAG_NAN);
+}
+
+template <typename Real>
+__global__ void __launch_bounds__(256)
+k_su_boundary(int nb, DevParams P, const int32_t *__restrict__ bstart, Real *__restrict__ rho,
+              Real *__restrict__ rhom, const Real *__restrict__ bar, Scalars *sc)
+{
+    __shared__ double sdt;
+    __shared__ int seuler;
+    if (threadIdx.x == 0) {
+        sdt = step_dt(P, sc);
+        seuler = ((sc->step + 1) % P.euler_every) == 0;
+    }
+    __syncthreads();
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb || i >= bstart[P.ncells]) return;
+    const Real dtr = (Real)sdt;
+    Real r = rho[i];
+    Real nr = seuler ? r + dtr * bar[i] : rhom[i] + (Real)(2.0 * sdt) * bar[i];
+    if (P.clamp && nr < (Real)P.rho0) nr = (Real)P.rho0;
+    rhom[i] = r;
+    rho[i] = nr;
+    if (!(nr == nr)) atomicOr(&sc->flags, SPH_FLAG_NAN);
+}
+
+__global__ void k_finalize(DevParams P, Scalars *sc)
+{
+    double dt = step_dt(P, sc);
+    sc->dt_last = dt;
+    sc->time += dt;
+    sc->step += 1;
+    sc->mx.f2 = 0ull;
+    sc->mx.c = 0ull;
+    sc->mx.visc = 0ull;
+    if (!(dt >= 1e-12)) atomicOr(&sc->flags, SPH_FLAG_DT_TOO_SMALL);
+}
+
+template <typename Real>
+static int su_t(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    int nf = (int)ctx->nf, nb = (int)ctx->nb;
+    int c = ctx->cur;
+    const int T = 256;
+    if (nf > 0)
+        SPH_LAUNCH(ctx, k_su_fluid<Real>, (nf + T - 1) / T, T, 0, st, nf, ctx->dp, w.fstart,
+                   w.x[c], w.y[c], w.z[c], (Real *)w.vx[c], (Real *)w.vy[c], (Real *)w.vz[c],
+                   (Real *)w.vmx[c], (Real *)w.vmy[c], (Real *)w.vmz[c], (Real *)w.rho[c],
+                   (Real *)w.rhom[c], (const typename V4T<Real>::T *)w.acc, w.sc);
+    if (nb > 0)
+        SPH_LAUNCH(ctx, k_su_boundary<Real>, (nb + T - 1) / T, T, 0, st, nb, ctx->dp, w.bstart,
+                   (Real *)w.brho, (Real *)w.brhom, (const Real *)w.bar, w.sc);
+    SPH_LAUNCH(ctx, k_finalize, 1, 1, 0, st, ctx->dp, w.sc);
+    return check_cuda(cudaGetLastError());
+}
+
+int su_launch(sph_ctx *ctx)
+{
+    if (ctx->precision == SPH_FP32_SPLIT) return su_t<float>(ctx);
+    return su_t<double>(ctx);
+}
+
+}  // namespace sph

@@ -1,0 +1,58 @@
+"""The C-ABI library loads on a CPU-only host and exports every call that
+include/sph.h declares (no compute calls without a GPU)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared(header):
+    src = open(os.path.join(ROOT, "include", header)).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(sph_[a-z_0-9]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libsph():
+    from paper_1110_3711_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_every_declared_symbol_is_exported(libsph):
+    names = _declared("sph.h")
+    assert "sph_interact" in names and "sph_create" in names
+    for n in names:
+        assert hasattr(libsph, n), n
+
+
+def test_binding_covers_header():
+    from paper_1110_3711_gb300 import sph
+    assert set(_declared("sph.h")) == set(sph.exported_symbols())
+
+
+def test_error_strings_and_workspace_on_cpu(libsph):
+    from paper_1110_3711_gb300 import sph
+    from sphcases import dam_break
+    assert sph.lib().sph_error_string(-6).decode().startswith("call out of order")
+    c = dam_break(0.02)
+    p = sph.make_params(c.params, "fp32")
+    ws = sph.sph_workspace_bytes(p, c.n_f, c.n_b)
+    p64 = sph.make_params(c.params, "fp64")
+    assert sph.sph_workspace_bytes(p64, c.n_f, c.n_b) > ws > c.n * 100
+    bad = sph.make_params(c.params, "fp32")
+    bad.cell_size = c.params.h  # below the support 2h
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(bad, c.n_f, c.n_b)
+
+
+def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
+    """The binding refuses to run when libsph.so is missing."""
+    from paper_1110_3711_gb300 import sph, build
+    monkeypatch.setattr(build, "LIB", str(tmp_path / "missing.so"))
+    monkeypatch.setattr(sph, "_lib", None)
+    with pytest.raises(RuntimeError):
+        sph.lib()

@@ -1,0 +1,227 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+Bars: the neighbour list (sorted ids, cells, CellBeginEnd) bit-exact; the
+exact work counts bit-exact; PI in SPH_FP64 within 1e-12 relative; the FP64
+time loop within the tolerances below after 100 steps; the FP32 split form
+within its float32 budget.  Sizes span many cells, tiles of the radix sort and
+a ragged tail.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from sphcases import dam_break, random_cloud, uniform_block
+from tests.gpu_common import need_gpu, make_sim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return need_gpu()
+
+
+@pytest.fixture(scope="module")
+def O():
+    from oracle import oracle
+    oracle.lib()
+    return oracle
+
+
+def _oracle_fluid_list(O, case, pos):
+    p = case.params
+    cell = O.cells(p, pos[:case.n_f])
+    order, start = O.cell_list(p, cell)
+    return cell, order, start
+
+
+def _check_nl(O, sim, case, pos):
+    ids, cell, start = sim.neighbour_list_arrays()
+    ocell, oorder, ostart = _oracle_fluid_list(O, case, pos)
+    assert np.array_equal(ids.astype(np.int64), oorder)
+    assert np.array_equal(cell.astype(np.int64), ocell[oorder])
+    assert np.array_equal(start.astype(np.int64), ostart)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_nl_bit_exact_dam_break(torch_mod, O, precision):
+    c = dam_break(0.02)
+    sim = make_sim(c, precision)
+    sim.neighbour_list()
+    _check_nl(O, sim, c, c.pos)
+
+
+@pytest.mark.parametrize("n,seed", [(1, 0), (31, 1), (2047, 2), (2049, 3), (50000, 4)])
+def test_nl_bit_exact_random(torch_mod, O, n, seed):
+    """Random order and positions, sizes around the radix tile (2048)."""
+    c = random_cloud(n + 17, box=0.3, dp=0.01, n_b=17, seed=seed)
+    sim = make_sim(c, "fp64")
+    sim.neighbour_list()
+    _check_nl(O, sim, c, c.pos)
+
+
+def test_nl_after_motion_and_out_of_grid(torch_mod, O):
+    """Positions that are not in lattice order, some outside the grid (they sort
+    last with the sentinel cell and raise the out-of-grid flag)."""
+    c = dam_break(0.02)
+    rng = np.random.default_rng(9)
+    pos = c.pos.copy()
+    pos[:c.n_f] += rng.normal(0, 0.3 * c.params.dp, size=(c.n_f, 3))
+    pos[5] = [-5.0, 0.1, 0.1]
+    pos[77] = [0.2, 0.2, 50.0]
+    c2 = type(c)(**{**c.__dict__, "pos": pos})
+    sim = make_sim(c2, "fp64")
+    sim.neighbour_list()
+    _check_nl(O, sim, c2, pos)
+    from paper_1110_3711_gb300.sph import FLAG_OUT_OF_GRID
+    assert sim.status(clear=True) & FLAG_OUT_OF_GRID
+
+
+def test_work_counts_exact(torch_mod, O):
+    c = dam_break(0.02)
+    sim = make_sim(c, "fp32")
+    sim.neighbour_list()
+    got = sim.count_work()
+    _, _, _, counts, _ = O.interact(c.params, c.n_f, c.n_b, c.pos, c.vel, c.rho)
+    assert np.array_equal(got, counts)
+
+
+def _random_state(case, seed=0):
+    rng = np.random.default_rng(seed)
+    vel = case.vel.copy()
+    vel[:case.n_f] = rng.normal(0, 0.3, size=(case.n_f, 3))
+    rho = case.rho * (1 + rng.normal(0, 2e-3, size=case.n))
+    return vel, rho
+
+
+@pytest.mark.parametrize("case_fn", [lambda: dam_break(0.02),
+                                     lambda: random_cloud(3000, box=0.1, dp=0.008, n_b=700, seed=5)])
+def test_pi_fp64_matches_oracle(torch_mod, O, case_fn):
+    c = case_fn()
+    vel, rho = _random_state(c, 1)
+    c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho})
+    sim = make_sim(c2, "fp64")
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(c.params, c.n_f, c.n_b, c.pos, vel, rho)
+    sa = np.abs(oace).max()
+    sr = np.abs(oar).max()
+    assert np.abs(ace - oace).max() <= 1e-12 * sa
+    assert np.abs(ar - oar).max() <= 1e-12 * sr
+    assert mx[2] == pytest.approx(ovm, rel=1e-13)
+    assert mx[0] == pytest.approx(np.sqrt((oace ** 2).sum(1)).max(), rel=1e-13)
+    assert mx[1] == pytest.approx(max(O.sound(c.params, r) for r in rho), rel=1e-13)
+
+
+def test_pi_fp32_split_matches_oracle(torch_mod, O):
+    """float32 PI on cell-relative offsets: errors relative to the force scale
+    (|g| + max|ace|) within 2e-5 and density rates within 2e-5 of their scale."""
+    c = dam_break(0.01)
+    vel, rho = _random_state(c, 2)
+    c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho})
+    sim = make_sim(c2, "fp32")
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(c.params, c.n_f, c.n_b, c.pos, vel, rho)
+    ea = np.abs(ace - oace).max() / (9.81 + np.abs(oace).max())
+    er = np.abs(ar - oar).max() / np.abs(oar).max()
+    assert ea < 2e-5, ea
+    assert er < 2e-5, er
+    assert mx[2] == pytest.approx(ovm, rel=1e-5)
+
+
+def test_fp64_time_loop_matches_oracle(torch_mod, O):
+    """100 steps of the 3D dam break at dp = 0.02 (about 10k fluid particles)."""
+    c = dam_break(0.02)
+    sim = make_sim(c, "fp64")
+    st = O.State(c)
+    steps = 100
+    dts_g, dts_o = [], []
+    for _ in range(steps):
+        dts_g.append(sim.step(want_dt=True))
+        dts_o.append(st.step(nthreads=8))
+    assert np.allclose(dts_g, dts_o, rtol=1e-9, atol=0)
+    pos, vel, rho = sim.get_state()
+    t = sum(dts_o)
+    dp = c.params.dp
+    vscale = np.abs(st.vel).max() + 9.81 * t
+    assert np.abs(pos - st.pos).max() <= 1e-9 * dp
+    assert np.abs(vel - st.vel).max() <= 1e-9 * vscale
+    assert np.abs(rho / st.rho - 1).max() <= 1e-9
+    tt, last, nsteps = sim.time()
+    assert nsteps == steps and tt == pytest.approx(t, rel=1e-12)
+
+
+def test_fp32_split_time_loop_error_budget(torch_mod, O):
+    """SPH_FP32_SPLIT against the FP64 oracle after 100 steps."""
+    c = dam_break(0.02)
+    sim = make_sim(c, "fp32")
+    st = O.State(c)
+    for _ in range(100):
+        sim.step()
+        st.step(nthreads=8)
+    pos, vel, rho = sim.get_state()
+    t = st.time
+    dp = c.params.dp
+    vscale = np.abs(st.vel).max() + 9.81 * t
+    assert np.abs(pos - st.pos).max() <= 1e-4 * dp
+    assert np.abs(vel - st.vel).max() <= 1e-3 * vscale
+    assert np.abs(rho / st.rho - 1).max() <= 1e-5
+
+
+def test_state_roundtrip_and_checkpoint(torch_mod, O):
+    torch = torch_mod
+    c = dam_break(0.02)
+    sim = make_sim(c, "fp32")
+    sim.run(7)
+    s1 = sim.get_state(with_prev=True)
+    buf = torch.empty(sim.checkpoint_bytes(), dtype=torch.uint8, device="cuda")
+    sim.save_state(buf)
+    sim.run(5)
+    s2 = sim.get_state()
+    sim.load_state(buf)
+    sim.run(5)
+    s3 = sim.get_state()
+    for a, b in zip(s2, s3):
+        assert np.array_equal(a, b)
+    # set_state with the previous level reproduces the same continuation
+    sim2 = make_sim(c, "fp32")
+    sim2.set_state(*s1)
+    sim2.run(5)
+    s4 = sim2.get_state()
+    # the step counter differs (Euler parity); 7 + 5 < 40 so both are Verlet
+    for a, b in zip(s2, s4):
+        assert np.array_equal(a, b)
+
+
+def test_no_boundary_and_no_fluid(torch_mod, O):
+    c = uniform_block(9, 0.01, seed=1, vel_sigma=0.2, rho_sigma=0.002)
+    sim = make_sim(c, "fp64")
+    sim.neighbour_list(); sim.interact()
+    ace, ar, _ = sim.forces()
+    oace, oar, _, _, _ = O.interact(c.params, c.n_f, 0, c.pos, c.vel, c.rho)
+    assert np.abs(ace - oace).max() <= 1e-12 * np.abs(oace).max()
+    # boundary only: nothing moves and no density changes
+    b = random_cloud(500, box=0.05, dp=0.01, n_b=500, seed=2)
+    simb = make_sim(b, "fp32")
+    simb.step()
+    pos, vel, rho = simb.get_state()
+    assert np.array_equal(pos, b.pos) and (rho >= 1000.0).all()
+
+
+def test_invalid_arguments_rejected(torch_mod):
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    p = sph.make_params(c.params, "fp32")
+    p.h = -1.0
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(p, c.n_f, c.n_b)
+    p = sph.make_params(c.params, "fp32")
+    sim = make_sim(c, "fp32")
+    with pytest.raises(sph.SphError):
+        sph.sph_interact(sim.ctx)   # PI before NL
+    with pytest.raises(sph.SphError):
+        sph.sph_create(p, c.n_f, c.n_b, c.pos, c.vel, c.rho, sim.workspace.data_ptr(), 16, None)
