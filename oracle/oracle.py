@@ -67,6 +67,9 @@ def lib():
             L.or_pairs.argtypes = [pp, i64, i64, vp, vp, vp, i64, vp]; L.or_pairs.restype = C.c_int
             L.or_interact.argtypes = [pp, i64, i64, vp, vp, vp, vp, vp, vp, vp, C.c_int]
             L.or_interact.restype = i64
+            L.or_interact_sampled.argtypes = [pp, i64, i64, vp, vp, vp, vp, vp, vp, vp, C.c_int,
+                                              i64, vp]
+            L.or_interact_sampled.restype = i64
             L.or_dt.argtypes = [pp, i64, i64, vp, vp, vp, d]; L.or_dt.restype = d
             L.or_update.argtypes = [pp, i64, i64, i64, d, vp, vp, vp, vp, vp, vp, vp]
             L.or_update.restype = None
@@ -174,6 +177,38 @@ def interact(p, n_f, n_b, pos, vel, rho, nthreads=0):
     if nout < 0:
         raise MemoryError("or_interact")
     return ace[:n_f], ar[:n], float(vm[0]), counts, int(nout)
+
+
+def interact_sampled(p, n_f, n_b, pos, vel, rho, stride, nthreads=0):
+    """PI on every stride-th target; returns (ace, ar, viscdt_max, counts, n_out,
+    seconds[2] = list build, interaction loop)."""
+    pos = np.ascontiguousarray(pos, np.float64)
+    vel = np.ascontiguousarray(vel, np.float64)
+    rho = np.ascontiguousarray(rho, np.float64)
+    n = n_f + n_b
+    ace = np.zeros((max(n_f, 1), 3), np.float64)
+    ar = np.zeros(max(n, 1), np.float64)
+    vm = np.zeros(1, np.float64)
+    counts = np.zeros(4, np.int64)
+    secs = np.zeros(2, np.float64)
+    nout = lib().or_interact_sampled(C.byref(params(p)), n_f, n_b, _ptr(pos), _ptr(vel), _ptr(rho),
+                                     _ptr(ace), _ptr(ar), _ptr(vm), _ptr(counts), int(nthreads),
+                                     int(stride), _ptr(secs))
+    if nout < 0:
+        raise MemoryError("or_interact_sampled")
+    return ace[:n_f], ar[:n], float(vm[0]), counts, int(nout), secs
+
+
+def update(p, n_f, n_b, step, dt, pos, vel, velm1, rho, rhom1, ace, ar):
+    """SU in place on the given arrays."""
+    ace = np.ascontiguousarray(ace, np.float64).reshape(-1)
+    if ace.size == 0:
+        ace = np.zeros(3, np.float64)
+    for a in (pos, vel, velm1, rho, rhom1):
+        assert a.flags["C_CONTIGUOUS"] and a.dtype == np.float64
+    lib().or_update(C.byref(params(p)), n_f, n_b, int(step), float(dt), _ptr(pos), _ptr(vel),
+                    _ptr(velm1), _ptr(rho), _ptr(rhom1), _ptr(ace),
+                    _ptr(np.ascontiguousarray(ar, np.float64)))
 
 
 def time_step(p, n_f, n_b, pos, ace, rho, viscdt_max):

@@ -278,19 +278,29 @@ int or_pairs(const or_params *p, int64_t nf, int64_t nb, const double *pos,
     return 0;
 }
 
-/* PI for all particles.  Outputs (id order): ace[3*nf] (fluid acceleration
+/* PI for the targets a with a % stride == 0 (stride 1: all particles; a
+ * larger stride times a uniform sample of the targets, the others get zero
+ * outputs).  seconds (may be NULL) receives the wall time of the list build
+ * and of the interaction loop.  Outputs (id order): ace[3*nf] (fluid acceleration
  * including gravity), ar[nf + nb] (density rate), the largest viscous term and
  * work counts: counts[0] candidates visited by fluid targets, counts[1] their
  * pairs, counts[2] candidates of boundary targets, counts[3] their pairs.
  * A candidate is a particle of the 27 cells (other than the target).
  * Returns the number of particles outside the cell grid. */
-int64_t or_interact(const or_params *p, int64_t nf, int64_t nb,
-                    const double *pos, const double *vel, const double *rho,
-                    double *ace, double *ar, double *viscdt_max, int64_t *counts,
-                    int nthreads)
+int64_t or_interact_sampled(const or_params *p, int64_t nf, int64_t nb,
+                            const double *pos, const double *vel, const double *rho,
+                            double *ace, double *ar, double *viscdt_max, int64_t *counts,
+                            int nthreads, int64_t stride, double *seconds)
 {
     or_lists L;
+#ifdef _OPENMP
+    double t0 = omp_get_wtime();
+#endif
     if (lists_build(p, nf, nb, pos, &L)) return -1;
+#ifdef _OPENMP
+    double t1 = omp_get_wtime();
+#endif
+    if (stride < 1) stride = 1;
     int64_t n = nf + nb;
     double *P = (double *)malloc(sizeof(double) * (size_t)(n + 1));
     double *C = (double *)malloc(sizeof(double) * (size_t)(n + 1));
@@ -308,7 +318,7 @@ int64_t or_interact(const or_params *p, int64_t nf, int64_t nb,
         int fluid = a < nf;
         double acc[3] = {0.0, 0.0, 0.0}, dr = 0.0, vm = 0.0;
         int64_t ncand = 0, npair = 0;
-        if (c < L.nc) {
+        if (c < L.nc && a % stride == 0) {
             const double *xa = pos + 3 * a;
             const double *va = vel + 3 * a;
 #define OR_PI_BODY                                                                  \
@@ -348,7 +358,22 @@ int64_t or_interact(const or_params *p, int64_t nf, int64_t nb,
     if (counts) { counts[0] = cf; counts[1] = pf; counts[2] = cb; counts[3] = pbn; }
     free(P); free(C);
     lists_free(&L);
+#ifdef _OPENMP
+    if (seconds) { seconds[0] = t1 - t0; seconds[1] = omp_get_wtime() - t1; }
+#else
+    if (seconds) { seconds[0] = 0.0; seconds[1] = 0.0; }
+#endif
     return nout;
+}
+
+/* PI for every target (see or_interact_sampled, stride 1). */
+int64_t or_interact(const or_params *p, int64_t nf, int64_t nb,
+                    const double *pos, const double *vel, const double *rho,
+                    double *ace, double *ar, double *viscdt_max, int64_t *counts,
+                    int nthreads)
+{
+    return or_interact_sampled(p, nf, nb, pos, vel, rho, ace, ar, viscdt_max, counts,
+                               nthreads, 1, NULL);
 }
 
 /* Variable time step (Monaghan & Kos 1999; Table 1; the maxima of Section

@@ -151,7 +151,10 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.val_tmp = b.take<uint32_t>(m);
     W.key_sorted = b.take<uint32_t>(m);
     W.val_sorted = b.take<uint32_t>(m);
-    W.count = b.take<uint32_t>((size_t)*ncells + 2);
+    W.count = b.take<uint32_t>((size_t)*ncells + 2 + kCtrWords);
+    W.ctr = W.count ? W.count + *ncells + 2 : nullptr;
+    W.items_f = b.take<uint32_t>(nf > 0 ? nf : 1);
+    W.items_b = b.take<uint32_t>(nb > 0 ? nb : 1);
     W.fstart = b.take<int32_t>((size_t)*ncells + 2);
     W.bstart = b.take<int32_t>((size_t)*ncells + 2);
     int64_t hist = (int64_t)256 * radix_tiles(m > 0 ? m : 1);
@@ -220,20 +223,24 @@ __global__ void k_gather_out(int nf, int nb, size_t N, double *__restrict__ stag
 }
 
 template <typename V4, typename Real>
-__global__ void k_export_forces(int nf, int nb, size_t N, const V4 *__restrict__ acc,
+__global__ void k_export_forces(int nf, int nb, size_t N, uint32_t ncells, const V4 *__restrict__ acc,
                                 const Real *__restrict__ bar, const uint32_t *__restrict__ id,
-                                const uint32_t *__restrict__ bid, double *__restrict__ stage)
+                                const uint32_t *__restrict__ bid, const uint32_t *__restrict__ cell,
+                                const uint32_t *__restrict__ bcell, double *__restrict__ stage)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double *ace = stage, *ar = stage + 3 * N;
     if (i < nf) {
         size_t k = id[i];
         V4 a = acc[i];
-        ace[3 * k] = (double)a.x; ace[3 * k + 1] = (double)a.y; ace[3 * k + 2] = (double)a.z;
-        ar[k] = (double)a.w;
+        bool in = cell[i] < ncells;   // particles outside the grid have no forces
+        ace[3 * k] = in ? (double)a.x : 0.0;
+        ace[3 * k + 1] = in ? (double)a.y : 0.0;
+        ace[3 * k + 2] = in ? (double)a.z : 0.0;
+        ar[k] = in ? (double)a.w : 0.0;
     } else if (i < nf + nb) {
         int j = i - nf;
-        ar[bid[j]] = (double)bar[j];
+        ar[bid[j]] = bcell[j] < ncells ? (double)bar[j] : 0.0;
     }
 }
 
@@ -363,6 +370,7 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b, const double *pos,
     cudaGetDevice(&ctx->device);
     plan_workspace(*p, n_f, n_b, dims, &nc, &ctx->w, (char *)workspace);
     rc = check_cuda(cudaMemsetAsync(ctx->w.sc, 0, sizeof(Scalars), ctx->stream));
+    if (!rc && ctx->precision == SPH_FP32_SPLIT) rc = pi32_setup(ctx);
     if (!rc) rc = load_state(ctx, pos, vel, rho, nullptr, nullptr);
     if (rc) {
         free(ctx);
@@ -502,12 +510,12 @@ int sph_get_forces(sph_ctx *ctx, double *ace, double *ar, double *maxima)
     if (N > 0) {
         if (ctx->precision == SPH_FP32_SPLIT)
             SPH_LAUNCH(ctx, (k_export_forces<float4, float>), (unsigned)((N + T - 1) / T), T, 0, st,
-                       nf, nb, N, (const float4 *)w.acc, (const float *)w.bar, w.id[ctx->cur],
-                       w.bid, w.stage);
+                       nf, nb, N, ctx->ncells, (const float4 *)w.acc, (const float *)w.bar,
+                       w.id[ctx->cur], w.bid, w.cell, w.bcell, w.stage);
         else
             SPH_LAUNCH(ctx, (k_export_forces<double4_32a, double>), (unsigned)((N + T - 1) / T), T, 0,
-                       st, nf, nb, N, (const double4_32a *)w.acc, (const double *)w.bar,
-                       w.id[ctx->cur], w.bid, w.stage);
+                       st, nf, nb, N, ctx->ncells, (const double4_32a *)w.acc, (const double *)w.bar,
+                       w.id[ctx->cur], w.bid, w.cell, w.bcell, w.stage);
     }
     int rc = copy_out(ace, w.stage, 3 * (size_t)nf * sizeof(double), st);
     if (!rc) rc = copy_out(ar, w.stage + 3 * N, N * sizeof(double), st);

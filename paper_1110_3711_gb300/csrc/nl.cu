@@ -353,15 +353,19 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
           typename Vec4<Real>::T *__restrict__ posp, typename Vec4<Real>::T *__restrict__ velr,
           uint32_t *__restrict__ cell, const Real *__restrict__ brho,
           typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
-          const int32_t *__restrict__ bstart, Scalars *sc)
+          const int32_t *__restrict__ bstart, const int32_t *__restrict__ fstart,
+          uint32_t *__restrict__ items, uint32_t *__restrict__ ctr, Scalars *sc)
 {
     __shared__ double red[32];
     typedef typename Vec4<Real>::T V4;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double cmax = 0.0;
+    bool item = false;
     if (i < nf) {
         uint32_t s = val_sorted[i];
         uint32_t c = key_sorted[i];
+        // a PI work item starts at every 32nd particle of a cell
+        if (SPLIT && c < P.ncells) item = ((i - fstart[c]) & 31) == 0;
         double x = sx[s], y = sy[s], z = sz[s];
         Real vx = svx[s], vy = svy[s], vz = svz[s];
         Real rho = srho[s];
@@ -408,6 +412,17 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
             }
             bposp[j] = pp;
             bvelr[j] = vv;
+        }
+    }
+    if (SPLIT) {
+        // warp-aggregated append of the work items (their order does not matter)
+        unsigned ball = __ballot_sync(0xffffffffu, item);
+        if (ball) {
+            int lane = threadIdx.x & 31;
+            uint32_t base = 0;
+            if (lane == 0) base = atomicAdd(&ctr[0], (uint32_t)__popc(ball));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
         }
     }
     block_max_to(&sc->mx.c, cmax, red);
@@ -480,7 +495,7 @@ static int nl_fluid_t(sph_ctx *ctx)
     int nf = (int)ctx->nf, nb = (int)ctx->nb;
     int src = ctx->cur, dst = 1 - ctx->cur;
     const int T = 256;
-    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2), st)))
+    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2 + kCtrReset), st)))
         return SPH_ERR_CUDA;
     if (nf > 0) {
         SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src],
@@ -503,7 +518,7 @@ static int nl_fluid_t(sph_ctx *ctx)
                    (Real *)w.vmy[dst], (Real *)w.vmz[dst], (Real *)w.rho[dst], (Real *)w.rhom[dst],
                    w.id[dst], (typename Vec4<Real>::T *)w.posp, (typename Vec4<Real>::T *)w.velr,
                    w.cell, (const Real *)w.brho, (typename Vec4<Real>::T *)w.bposp,
-                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.sc);
+                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.fstart, w.items_f, w.ctr, w.sc);
     }
     ctx->cur = dst;
     return check_cuda(cudaGetLastError());
@@ -528,7 +543,7 @@ static int nl_boundary_t(sph_ctx *ctx)
     const double *in_rho = w.stage + 6 * N;
     const double *in_rhom = w.stage + 10 * N;
     const int T = 256;
-    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2), st)))
+    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2 + kCtrWords), st)))
         return SPH_ERR_CUDA;
     if (nb > 0) {
         SPH_LAUNCH(ctx, k_boundary_hash, (nb + T - 1) / T, T, 0, st, in_pos, (uint32_t)nf, nb,
@@ -544,6 +559,10 @@ static int nl_boundary_t(sph_ctx *ctx)
     int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.bstart, (int64_t)ctx->ncells + 2,
                                 w.scan_part, st);
     if (rc) return rc;
+    if (SPLIT) {
+        rc = boundary_items_launch(ctx);
+        if (rc) return rc;
+    }
     return check_cuda(cudaGetLastError());
 }
 

@@ -162,130 +162,6 @@ k_pi_boundary64(int nb, DevParams P, const double4_32a *__restrict__ bposp,
     block_max_to(&sc->mx.visc, vis, red);
 }
 
-// ------------------------------------------------------------------ FP32 --
-
-struct Acc32 {
-    float ax, ay, az, ar, vis;
-};
-
-template <bool MOMENTUM>
-__device__ __forceinline__ void pair32(const DevParams &P, const float4 &pa, const float4 &va,
-                                       float ca, const float4 &pb, const float4 &vb, float rx,
-                                       float ry, float rz, float r2, Acc32 &o)
-{
-    float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-    float r = r2 * rinv;
-    float q = r * P.invhf;
-    float t = 2.0f - q;
-    float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
-    float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
-    float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
-    float mu = __fdividef(P.hf * vdr, r2 + P.eta2f);
-    if (MOMENTUM) {
-        float rb = vb.w * P.inv_rho0f;
-        float cb = P.c0f * rb * rb * rb;
-        float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
-        float coef = -(pa.w + pb.w + Pi) * F;
-        o.ax = fmaf(coef, rx, o.ax);
-        o.ay = fmaf(coef, ry, o.ay);
-        o.az = fmaf(coef, rz, o.az);
-    }
-    o.ar = fmaf(vdr, F, o.ar);
-    o.vis = fmaxf(o.vis, fabsf(mu));
-}
-
-template <bool MOMENTUM>
-__device__ __forceinline__ void cells32(const DevParams &P, const float4 &pa, const float4 &va,
-                                        float ca, int cx, int cy, int cz,
-                                        const float4 *__restrict__ posp,
-                                        const float4 *__restrict__ velr,
-                                        const int32_t *__restrict__ start, Acc32 &o)
-{
-    for (int dz = -1; dz <= 1; ++dz) {
-        int z = cz + dz;
-        if (z < 0 || z >= P.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
-            int y = cy + dy;
-            if (y < 0 || y >= P.ny) continue;
-            int row = P.nx * (y + P.ny * z);
-            for (int dx = -1; dx <= 1; ++dx) {
-                int x = cx + dx;
-                if (x < 0 || x >= P.nx) continue;
-                int j0 = start[row + x], j1 = start[row + x + 1];
-                // target position relative to the candidate cell's origin
-                float xa = pa.x - (float)dx * P.sf;
-                float ya = pa.y - (float)dy * P.sf;
-                float za = pa.z - (float)dz * P.sf;
-                for (int j = j0; j < j1; ++j) {
-                    float4 pb = posp[j];
-                    float rx = xa - pb.x, ry = ya - pb.y, rz = za - pb.z;
-                    float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-                    if (r2 < P.four_h2f) pair32<MOMENTUM>(P, pa, va, ca, pb, velr[j], rx, ry, rz, r2, o);
-                }
-            }
-        }
-    }
-}
-
-__global__ void __launch_bounds__(128)
-k_pi_fluid32(int nf, DevParams P, const float4 *__restrict__ posp, const float4 *__restrict__ velr,
-             const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
-             const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
-             const int32_t *__restrict__ bstart, float4 *__restrict__ acc, Scalars *sc)
-{
-    __shared__ double red[32];
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int nvalid = fstart[P.ncells];
-    double f2 = 0.0, vis = 0.0;
-    if (i < nvalid) {
-        float4 pa = posp[i], va = velr[i];
-        int cx, cy, cz;
-        cell_xyz(P, cell[i], &cx, &cy, &cz);
-        float ra = va.w * P.inv_rho0f;
-        float ca = P.c0f * ra * ra * ra;
-        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        // the self pair has r_ab = 0 and v_ab = 0 and adds exactly zero
-        cells32<true>(P, pa, va, ca, cx, cy, cz, posp, velr, fstart, o);
-        cells32<true>(P, pa, va, ca, cx, cy, cz, bposp, bvelr, bstart, o);
-        float ax = fmaf(P.massf, o.ax, P.gf[0]);
-        float ay = fmaf(P.massf, o.ay, P.gf[1]);
-        float az = fmaf(P.massf, o.az, P.gf[2]);
-        acc[i] = make_float4(ax, ay, az, P.massf * o.ar);
-        f2 = (double)ax * ax + (double)ay * ay + (double)az * az;
-        vis = (double)o.vis;
-        if (!(f2 < INFINITY) || !(o.ar == o.ar)) atomicOr(&sc->flags, SPH_FLAG_NAN);
-    } else if (i < nf) {
-        acc[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    block_max_to(&sc->mx.f2, f2, red);
-    block_max_to(&sc->mx.visc, vis, red);
-}
-
-__global__ void __launch_bounds__(128)
-k_pi_boundary32(int nb, DevParams P, const float4 *__restrict__ bposp,
-                const float4 *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
-                const int32_t *__restrict__ bstart, const float4 *__restrict__ posp,
-                const float4 *__restrict__ velr, const int32_t *__restrict__ fstart,
-                float *__restrict__ bar, Scalars *sc)
-{
-    __shared__ double red[32];
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    int nvalid = bstart[P.ncells];
-    double vis = 0.0;
-    if (i < nvalid) {
-        float4 pa = bposp[i], va = bvelr[i];
-        int cx, cy, cz;
-        cell_xyz(P, bcell[i], &cx, &cy, &cz);
-        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        cells32<false>(P, pa, va, 0.f, cx, cy, cz, posp, velr, fstart, o);
-        bar[i] = P.massf * o.ar;
-        vis = (double)o.vis;
-    } else if (i < nb) {
-        bar[i] = 0.f;
-    }
-    block_max_to(&sc->mx.visc, vis, red);
-}
-
 // -------------------------------------------------------- validation pass --
 
 // Exact counts in float64 with the products and sums rounded one by one (no
@@ -358,16 +234,7 @@ int pi_launch(sph_ctx *ctx)
     int nf = (int)ctx->nf, nb = (int)ctx->nb;
     const int T = 128;
     if (ctx->precision == SPH_FP32_SPLIT) {
-        if (nf > 0)
-            SPH_LAUNCH(ctx, k_pi_fluid32, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
-                       (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc,
-                       w.sc);
-        if (nb > 0)
-            SPH_LAUNCH(ctx, k_pi_boundary32, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
-                       (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart, (float *)w.bar,
-                       w.sc);
+        return pi32_launch(ctx);
     } else {
         if (nf > 0)
             SPH_LAUNCH(ctx, k_pi_fluid64, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,

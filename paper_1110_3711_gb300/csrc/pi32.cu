@@ -1,0 +1,341 @@
+// PI stage, SPH_FP32_SPLIT form: warp-cooperative particle interaction.
+//
+// The paper's GPU kernel (Section 4, Fig. 11) gives every target particle its
+// own thread and its own walk over the 27 cells; the pair body then runs under
+// a divergent branch (a warp idles whenever any lane has a false neighbour,
+// Section 4 "code divergence").  Here one warp owns a work item: up to 32
+// target particles of one cell (cells follow X, Y, Z after NL, so they are a
+// contiguous range).  For that item the warp
+//   1. builds the table of its 9 fluid x-runs (and 9 boundary x-runs for
+//      fluid targets): cells x-1..x+1 of every (y, z) row are one index range
+//      (Section 4.4, Fig. 10);
+//   2. stages the candidates of those runs in shared memory, already shifted
+//      into the frame of the target cell (candidate offset + cell delta * s),
+//      with |x_b|^2 beside them;
+//   3. tests all candidates against all 32 targets in lockstep: the warp reads
+//      one candidate (a shared-memory broadcast) and each lane evaluates
+//      |x_b|^2 - 2 x_a.x_b < 4h^2 - |x_a|^2 (three FMAs and a compare, the same
+//      test as |x_a - x_b|^2 < 4h^2), collecting a hit bit per candidate;
+//   4. walks its own hit bits (about 112 real neighbours per lane, so lanes
+//      stay balanced) and evaluates the pair terms of the oracle (cubic-spline
+//      gradient, Tait pressure, artificial viscosity, continuity) from the
+//      staged data, recomputing r_ab exactly from the shifted offsets.
+// Work items are taken from a list built by NL with an atomic counter, so the
+// grid is persistent (one resident set of CTAs) and balances itself.  Sums of
+// a target are accumulated by one lane in candidate order, so results do not
+// depend on the order the items are processed in.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+#ifndef SPH_PI_CAP
+#define SPH_PI_CAP 256
+#endif
+#ifndef SPH_PI_WARPS
+#define SPH_PI_WARPS 4
+#endif
+#ifndef SPH_PI_MINB
+#define SPH_PI_MINB 1
+#endif
+
+namespace sph {
+
+namespace {
+
+constexpr int CAP = SPH_PI_CAP;   // staged candidates per warp and pass
+constexpr int NCH = CAP / 32;     // 32-candidate chunks per pass
+constexpr int WARPS = SPH_PI_WARPS;
+constexpr int NRUN = 18;          // 9 fluid + 9 boundary x-runs
+static_assert(CAP % 32 == 0, "CAP must be a multiple of 32");
+
+struct WarpSmem {
+    float4 A[CAP];        // shifted candidate offset {x, y, z} and |x|^2
+    float4 V[CAP];        // candidate {vx, vy, vz, rho}
+    float Pr[CAP];        // candidate P / rho^2
+    uint32_t M[NCH][32];  // hit bits of lane l for chunk q
+    int4 run[NRUN];       // {inclusive end slot, first index, start of cell x, start of cell x+1}
+    int code[NRUN];       // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
+};
+
+struct Acc {
+    float ax, ay, az, ar, vis;
+};
+
+// Terms of one ordered pair a <- b (see the oracle): momentum sum, continuity
+// sum and the viscous dt term.
+template <bool MOMENTUM>
+__device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, float za,
+                                     const float4 &pa, const float4 &va, float ca,
+                                     const float4 &b, const float4 &vb, float prb, Acc &o)
+{
+    float rx = xa - b.x, ry = ya - b.y, rz = za - b.z;
+    float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    float rinv = rsqrtf(fmaxf(r2, 1e-30f));
+    float r = r2 * rinv;
+    float q = r * P.invhf;
+    float t = fmaxf(2.0f - q, 0.0f);
+    float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
+    float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
+    float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
+    float mu = __fdividef(P.hf * vdr, r2 + P.eta2f);
+    if (MOMENTUM) {
+        float rb = vb.w * P.inv_rho0f;
+        float cb = P.c0f * rb * rb * rb;
+        float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
+        float coef = -(pa.w + prb + Pi) * F;
+        o.ax = fmaf(coef, rx, o.ax);
+        o.ay = fmaf(coef, ry, o.ay);
+        o.az = fmaf(coef, rz, o.az);
+    }
+    o.ar = fmaf(vdr, F, o.ar);
+    o.vis = fmaxf(o.vis, fabsf(mu));
+}
+
+// MOMENTUM: fluid targets (F-F and F-B, acc out).  !MOMENTUM: boundary targets
+// (B-F continuity only, bar out).
+template <bool MOMENTUM>
+__global__ void __launch_bounds__(WARPS * 32, SPH_PI_MINB)
+k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restrict__ n_items_p,
+       uint32_t *__restrict__ next_p, const float4 *__restrict__ tposp,
+       const float4 *__restrict__ tvelr, const uint32_t *__restrict__ tcell,
+       const int32_t *__restrict__ tstart, const float4 *__restrict__ fposp,
+       const float4 *__restrict__ fvelr, const int32_t *__restrict__ fstart,
+       const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
+       const int32_t *__restrict__ bstart, float4 *__restrict__ acc, float *__restrict__ bar,
+       Scalars *sc)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    WarpSmem &S = smem[threadIdx.x >> 5];
+    const uint32_t n_items = *n_items_p;
+    double f2max = 0.0;
+    float vismax = 0.0f;
+    bool bad = false;
+    const int nlists = MOMENTUM ? 2 : 1;
+
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(next_p, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+
+        // ---- the item: targets [i0, i0 + nt) of cell c
+        const int i0 = (int)items[it];
+        const uint32_t c = tcell[i0];
+        const int nt = min(32, tstart[c + 1] - i0);
+        const bool active = lane < nt;
+        const int i = i0 + (active ? lane : 0);
+        const float4 pa = tposp[i], va = tvelr[i];
+        const uint32_t cyz = c / (uint32_t)P.nx;
+        const int cx = (int)(c - cyz * (uint32_t)P.nx);
+        const int cy = (int)(cyz % (uint32_t)P.ny);
+        const int cz = (int)(cyz / (uint32_t)P.ny);
+        const float xa = pa.x, ya = pa.y, za = pa.z;
+        const float m2x = -2.0f * xa, m2y = -2.0f * ya, m2z = -2.0f * za;
+        const float thr = active ? P.four_h2f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
+        const float ra = va.w * P.inv_rho0f;
+        const float ca = P.c0f * ra * ra * ra;
+
+        // ---- run table: lane r describes run r
+        int K;
+        {
+            const int r = lane;
+            int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
+            if (r < 9 * nlists) {
+                const int list = r / 9, q = r % 9;
+                const int dz = q / 3 - 1, dy = q % 3 - 1;
+                const int y = cy + dy, z = cz + dz;
+                code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
+                if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
+                    const int32_t *st = list ? bstart : fstart;
+                    const int row = P.nx * (y + P.ny * z);
+                    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
+                    j0 = st[row + x0];
+                    L = st[row + x1 + 1] - j0;
+                    b1 = st[row + cx];
+                    b2 = st[row + cx + 1];
+                }
+            }
+            int pe = L;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, pe, o);
+                if (lane >= o) pe += t;
+            }
+            if (r < NRUN) {
+                S.run[r] = make_int4(pe, j0, b1, b2);
+                S.code[r] = code;
+            }
+            K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
+        }
+        __syncwarp();
+
+        Acc o = {0.f, 0.f, 0.f, 0.f, 0.f};
+        for (int base = 0; base < K; base += CAP) {
+            const int np = min(CAP, K - base);
+            const int nch = (np + 31) >> 5;
+            // ---- stage the candidates of this pass
+            int r = 0;
+            for (int m = 0; m < nch; ++m) {
+                const int ls = lane + 32 * m;
+                const int s = base + ls;
+                float4 a, v;
+                float pr;
+                if (s < K) {
+                    while (s >= S.run[r].x) ++r;
+                    const int4 ri = S.run[r];
+                    const int prev = r ? S.run[r - 1].x : 0;
+                    const int j = ri.y + (s - prev);
+                    const int cd = S.code[r];
+                    const float sx = j < ri.z ? -P.sf : (j < ri.w ? 0.0f : P.sf);
+                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.sf;
+                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.sf;
+                    float4 p;
+                    if (MOMENTUM && (cd & 1)) {
+                        p = bposp[j];
+                        v = bvelr[j];
+                    } else {
+                        p = fposp[j];
+                        v = fvelr[j];
+                    }
+                    a.x = p.x + sx;
+                    a.y = p.y + sy;
+                    a.z = p.z + sz;
+                    a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+                    pr = p.w;
+                } else {
+                    a = make_float4(0.f, 0.f, 0.f, INFINITY);
+                    v = make_float4(0.f, 0.f, 0.f, 1.f);
+                    pr = 0.f;
+                }
+                S.A[ls] = a;
+                S.V[ls] = v;
+                S.Pr[ls] = pr;
+            }
+            __syncwarp();
+            // ---- lockstep distance tests, one hit bit per candidate
+            for (int q = 0; q < nch; ++q) {
+                // four independent partial masks keep the 32 tests free of a
+                // serial dependency chain
+                uint32_t m4[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float4 a = S.A[q * 32 + k];
+                    const float t = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w)));
+                    m4[k & 3] |= (t < thr ? 1u : 0u) << k;
+                }
+                S.M[q][lane] = (m4[0] | m4[1]) | (m4[2] | m4[3]);
+            }
+            // ---- every lane walks its own hits (about 112 per lane in all)
+            int q = 0;
+            uint32_t m = S.M[0][lane];
+            for (;;) {
+                while (m == 0u && q + 1 < nch) {
+                    ++q;
+                    m = S.M[q][lane];
+                }
+                if (m == 0u) break;
+                const int ls = q * 32 + __ffs(m) - 1;
+                m &= m - 1u;
+                pair<MOMENTUM>(P, xa, ya, za, pa, va, ca, S.A[ls], S.V[ls], S.Pr[ls], o);
+            }
+            __syncwarp();
+        }
+
+        if (active) {
+            if (MOMENTUM) {
+                const float ax = fmaf(P.massf, o.ax, P.gf[0]);
+                const float ay = fmaf(P.massf, o.ay, P.gf[1]);
+                const float az = fmaf(P.massf, o.az, P.gf[2]);
+                const float ar = P.massf * o.ar;
+                acc[i] = make_float4(ax, ay, az, ar);
+                const double f2 = (double)ax * ax + (double)ay * ay + (double)az * az;
+                f2max = fmax(f2max, f2);
+                bad |= !(f2 < INFINITY) || !(ar == ar);
+            } else {
+                const float ar = P.massf * o.ar;
+                bar[i] = ar;
+                bad |= !(ar == ar);
+            }
+            vismax = fmaxf(vismax, o.vis);
+        }
+    }
+    if (bad) atomicOr(&sc->flags, SPH_FLAG_NAN);
+    if (MOMENTUM) block_max_to(&sc->mx.f2, f2max, red);
+    block_max_to(&sc->mx.visc, (double)vismax, red);
+}
+
+// Work items of the boundary list (built once): every 32nd particle of a cell.
+__global__ void k_boundary_items(int nb, DevParams P, const uint32_t *__restrict__ bcell,
+                                 const int32_t *__restrict__ bstart, uint32_t *__restrict__ items,
+                                 uint32_t *__restrict__ count)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    bool item = false;
+    if (i < nb && i < bstart[P.ncells]) {
+        uint32_t c = bcell[i];
+        item = ((i - bstart[c]) & 31) == 0;
+    }
+    unsigned ball = __ballot_sync(0xffffffffu, item);
+    if (ball) {
+        int lane = threadIdx.x & 31;
+        uint32_t base = 0;
+        if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(ball));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+    }
+}
+
+}  // namespace
+
+int pi32_setup(sph_ctx *ctx)
+{
+    int dev = 0, sms = 0, bf = 0, bb = 0;
+    if (check_cuda(cudaGetDevice(&dev))) return SPH_ERR_CUDA;
+    if (check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return SPH_ERR_CUDA;
+    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true>, WARPS * 32, 0)))
+        return SPH_ERR_CUDA;
+    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_pi32<false>, WARPS * 32, 0)))
+        return SPH_ERR_CUDA;
+    ctx->pi_grid_f = sms * (bf > 0 ? bf : 1);
+    ctx->pi_grid_b = sms * (bb > 0 ? bb : 1);
+    return SPH_OK;
+}
+
+int boundary_items_launch(sph_ctx *ctx)
+{
+    int nb = (int)ctx->nb;
+    if (nb == 0) return SPH_OK;
+    Workspace &w = ctx->w;
+    const int T = 256;
+    SPH_LAUNCH(ctx, k_boundary_items, (nb + T - 1) / T, T, 0, ctx->stream, nb, ctx->dp, w.bcell,
+               w.bstart, w.items_b, &w.ctr[3]);
+    return check_cuda(cudaGetLastError());
+}
+
+int pi32_launch(sph_ctx *ctx)
+{
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    // clear the two "next item" counters (fluid, boundary)
+    if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, 2 * sizeof(uint32_t), st))) return SPH_ERR_CUDA;
+    if (ctx->nf > 0)
+        SPH_LAUNCH(ctx, k_pi32<true>, ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp, w.items_f,
+                   &w.ctr[0], &w.ctr[1], (const float4 *)w.posp, (const float4 *)w.velr, w.cell,
+                   w.fstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
+                   (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc,
+                   (float *)nullptr, w.sc);
+    if (ctx->nb > 0)
+        SPH_LAUNCH(ctx, k_pi32<false>, ctx->pi_grid_b, WARPS * 32, 0, st, ctx->dp, w.items_b,
+                   &w.ctr[3], &w.ctr[2], (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell,
+                   w.bstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
+                   (const float4 *)nullptr, (const float4 *)nullptr, w.bstart, (float4 *)nullptr,
+                   (float *)w.bar, w.sc);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace sph

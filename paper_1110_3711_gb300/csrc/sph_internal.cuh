@@ -73,7 +73,9 @@ struct Workspace {
     size_t bstate_chunk_bytes;
     // NL scratch
     uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
-    uint32_t *count;          // [ncells + 2]
+    uint32_t *count;          // [ncells + 2], then the work-item counters ctr
+    uint32_t *ctr;            // [0] fluid items, [1] fluid next, [2] boundary next, [3] boundary items
+    uint32_t *items_f, *items_b;  // PI work items: first target index of a (cell, 32-target chunk)
     int32_t *fstart, *bstart; // [ncells + 2]
     uint32_t *radix_hist;     // [256 * tiles]
     uint32_t *scan_part;      // scan partials
@@ -100,6 +102,7 @@ struct sph_ctx {
     bool nl_valid, pi_valid;
     long long launches;
     int device;
+    int pi_grid_f, pi_grid_b;   // persistent grid sizes of the FP32 PI kernels
 };
 
 namespace sph {
@@ -115,9 +118,14 @@ void nl_boundary_refresh_launch(sph_ctx *ctx, cudaStream_t st);
 int radix_tiles(int64_t n);
 size_t scan_partials(int64_t n);
 
-// PI (pi.cu)
+// PI (pi.cu, pi32.cu)
 int pi_launch(sph_ctx *ctx);
+int pi32_launch(sph_ctx *ctx);
+int pi32_setup(sph_ctx *ctx);
+int boundary_items_launch(sph_ctx *ctx);
 int count_work_launch(sph_ctx *ctx);
+constexpr int kCtrWords = 4;     // work-item counters after the cell counts
+constexpr int kCtrReset = 3;     // counters cleared by every fluid NL
 
 // SU (su.cu)
 int su_launch(sph_ctx *ctx);
