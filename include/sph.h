@@ -183,6 +183,37 @@ int sph_checkpoint_bytes(const sph_ctx *ctx, size_t *bytes);
 int sph_save_state(sph_ctx *ctx, void *dst);
 int sph_load_state(sph_ctx *ctx, const void *src);
 
+/* Limits of sph_neighbour_list_static (points, cells of the grid). */
+#define SPH_STATIC_MAX_POINTS 524288
+#define SPH_STATIC_MAX_CELLS  16777216
+
+/* The neighbour list of one point set, computed without any device
+ * allocation.  The paper has no counterpart: this call is for callers that
+ * cannot call cudaMalloc -- a solver embedded in a host program whose own
+ * allocator owns all of the GPU's memory, or a loop that must not stall on
+ * cudaMalloc/cudaFree, which can synchronise the whole device.
+ *   p           run constants; only the cell grid (h, cell_size, dom_min,
+ *               dom_max) and the parameter checks of sph_workspace_bytes matter
+ *   n           number of points, at most SPH_STATIC_MAX_POINTS; the grid may
+ *               have at most SPH_STATIC_MAX_CELLS cells (else SPH_ERR_TOO_LARGE)
+ *   pos         [n][3] float64 positions in device memory of the current GPU
+ *   sorted_id   out, [n] uint32: the points in (cell, index) order
+ *   cell        out, [n] uint32: cell id of sorted_id[k] (n_cells if outside)
+ *   cell_start  out, [n_cells + 2] int32: number of points in cells below c
+ *               (the CellBeginEnd array of sph_get_neighbour_list)
+ *   stream      CUDA stream (NULL: legacy default stream); asynchronous.
+ * Every output is device memory the caller owns.  The same outputs as the fluid
+ * part of sph_neighbour_list for the same positions, bit for bit.
+ * Scratch: one fixed device array inside the library (about 8.7 MB), held by
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture.
+ * Every call shares the array and leaves its contents behind, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise them. */
+int sph_neighbour_list_static(const sph_params *p, int64_t n, const double *pos,
+                              uint32_t *sorted_id, uint32_t *cell, int32_t *cell_start,
+                              void *stream);
+
 /* Human-readable text of a return code (static storage). */
 const char *sph_error_string(int code);
 

@@ -101,6 +101,16 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
 
 }  // namespace
 
+int validate_params(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells)
+{
+    return validate(p, nf, nb, dims, ncells);
+}
+
+DevParams derive_params(const sph_params &p, const int dims[3], uint32_t ncells)
+{
+    return derive(p, dims, ncells);
+}
+
 size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells,
                       Workspace *w, char *base)
 {

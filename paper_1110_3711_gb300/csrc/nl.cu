@@ -70,6 +70,7 @@ constexpr int RS_THREADS = 256;
 constexpr int RS_WARPS = RS_THREADS / 32;
 constexpr int RS_IPT = 8;
 constexpr int RS_TILE = RS_THREADS * RS_IPT;
+static_assert(RS_TILE == kRadixTile, "tile size shared with the static-scratch neighbour list");
 
 int radix_tiles(int64_t n) { return (int)((n + RS_TILE - 1) / RS_TILE); }
 
@@ -250,7 +251,7 @@ int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
 
 // Sort (key, val) pairs of length n with `passes` 8-bit passes; the result is
 // in (kout, vout).  tmp buffers have length n.
-static int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t *ktmp,
+int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t *ktmp,
                       uint32_t *vtmp, uint32_t *kout, uint32_t *vout, int n, int passes,
                       cudaStream_t st)
 {
@@ -478,6 +479,8 @@ __global__ void k_boundary_hash(const double *__restrict__ pos, uint32_t nf, int
     atomicAdd(&count[c], 1u);
 }
 
+int key_passes_for(uint32_t ncells);
+
 static int key_passes(uint32_t ncells)
 {
     int bits = 0;
@@ -565,6 +568,8 @@ static int nl_boundary_t(sph_ctx *ctx)
     }
     return check_cuda(cudaGetLastError());
 }
+
+int key_passes_for(uint32_t ncells) { return key_passes(ncells); }
 
 int nl_boundary_build(sph_ctx *ctx)
 {

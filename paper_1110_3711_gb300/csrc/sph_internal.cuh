@@ -111,8 +111,18 @@ namespace sph {
 size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells,
                       Workspace *w, char *base);
 
+// parameter checks and derived constants (api.cu)
+int validate_params(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells);
+DevParams derive_params(const sph_params &p, const int dims[3], uint32_t ncells);
+
 // NL (nl.cu)
 int nl_fluid(sph_ctx *ctx);
+int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t *ktmp,
+               uint32_t *vtmp, uint32_t *kout, uint32_t *vout, int n, int passes,
+               cudaStream_t st);
+int key_passes_for(uint32_t ncells);
+__global__ void k_boundary_hash(const double *__restrict__ pos, uint32_t nf, int nb, DevParams P,
+                                uint32_t *key_by_id, uint32_t *val_by_id, uint32_t *count);
 int nl_boundary_build(sph_ctx *ctx);
 void nl_boundary_refresh_launch(sph_ctx *ctx, cudaStream_t st);
 int radix_tiles(int64_t n);
@@ -134,6 +144,7 @@ int su_launch(sph_ctx *ctx);
 int check_cuda(cudaError_t e);
 
 // generic helpers
+constexpr int kRadixTile = 2048;   // keys per radix-sort tile (nl.cu)
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanBlock * kScanItems;

@@ -97,6 +97,7 @@ def lib():
                 "sph_checkpoint_bytes": ([vp, C.POINTER(sz)], i32),
                 "sph_save_state": ([vp, vp], i32),
                 "sph_load_state": ([vp, vp], i32),
+                "sph_neighbour_list_static": ([pp, i64, vp, vp, vp, vp, vp], i32),
                 "sph_error_string": ([i32], C.c_char_p),
                 "sph_destroy": ([vp], None),
             }
@@ -114,7 +115,7 @@ def exported_symbols():
             "sph_update", "sph_run", "sph_get_state", "sph_set_state", "sph_get_time",
             "sph_status", "sph_get_neighbour_list", "sph_get_grid", "sph_get_forces",
             "sph_count_work", "sph_launch_count", "sph_checkpoint_bytes", "sph_save_state",
-            "sph_load_state", "sph_error_string", "sph_destroy"]
+            "sph_load_state", "sph_neighbour_list_static", "sph_error_string", "sph_destroy"]
 
 
 def _check(code, what):
@@ -264,6 +265,18 @@ def sph_save_state(ctx, dst):
 
 def sph_load_state(ctx, src):
     _check(lib().sph_load_state(ctx, _ptr(src)), "sph_load_state")
+
+
+STATIC_MAX_POINTS = 524288
+STATIC_MAX_CELLS = 16777216
+
+
+def sph_neighbour_list_static(p: sph_params, n, pos, sorted_id, cell, cell_start, stream=None):
+    """Neighbour list of n points with no device allocation (see include/sph.h):
+    pos and the three outputs are device arrays the caller owns."""
+    _check(lib().sph_neighbour_list_static(C.byref(p), int(n), _ptr(pos), _ptr(sorted_id),
+                                           _ptr(cell), _ptr(cell_start), stream),
+           "sph_neighbour_list_static")
 
 
 def sph_destroy(ctx):
