@@ -233,3 +233,10 @@ CONFIGS = {
                     vel_sigma=0.05, checkpoint_every=20),
     "dam20m": dict(dp=0.0016, steps=500, precision="fp32"),
 }
+
+
+def small_dam(dp: float = 0.02, *, seed: int = 0, vel_sigma: float = 0.05) -> Case:
+    """A small dam break (tank 0.3 x 0.12 x 0.24 m, column 0.1 x 0.12 x 0.12 m)
+    with a seeded velocity perturbation: the case the gradient oracle runs."""
+    return dam_break(dp, seed=seed, vel_sigma=vel_sigma, tank=(0.3, 0.12, 0.24),
+                     column=(0.1, 0.12, 0.12))
