@@ -183,6 +183,40 @@ int sph_checkpoint_bytes(const sph_ctx *ctx, size_t *bytes);
 int sph_save_state(sph_ctx *ctx, void *dst);
 int sph_load_state(sph_ctx *ctx, const void *src);
 
+/* ---- objective and adjoint (differentiable form) -------------------------
+ * An adjoint vector lam is float64 in persistent-id order with the layout of
+ * sph_get_state: [x: 3N][v: 3N][rho: N][v_prev: 3N][rho_prev: N], N = n_f + n_b
+ * (boundary rows of x, v and v_prev are unused).  It holds dJ/d(state) for a
+ * scalar objective J. */
+
+/* Maximum number of sensor points per call. */
+#define SPH_MAX_SENSORS 4096
+
+/* Pressure at sensor points (device [S][3] float64) for the current state,
+ * Shepard-normalised over the fluid particles within 2h:
+ *   P_s = sum_b (m/rho_b) P_b W_sb / sum_b (m/rho_b) W_sb   (0 with no particle),
+ * with the Tait pressure and cubic spline of Table 1.  Output: device [S].
+ * Requires sph_neighbour_list for the current state.  Asynchronous. */
+int sph_sensor_pressure(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
+                        double *pressure);
+
+/* Adds to lam (device, layout above) the derivative of J = sum_s dj_dp[s] P_s
+ * with respect to the current state's positions and densities.  SPH_FP64 only;
+ * requires sph_neighbour_list for the current state.  Asynchronous. */
+int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
+                       const double *dj_dp, double *lam);
+
+/* Adjoint of one time step at fixed dt (PI + SU, Table 1 formulation; the
+ * neighbour relation of the step is a constant of the step).  The context must
+ * hold the state at the start of the step (e.g. after sph_load_state of a
+ * snapshot taken then); the call rebuilds that step's neighbour list and PI
+ * (left valid, so sph_sensor_adjoint may follow), then writes to lam the adjoint
+ * of the state at the start of the step given lam_next, the adjoint of the state
+ * after it, and adds dJ/dalpha to *dalpha.  lam, lam_next and dalpha are device
+ * memory and must not alias.  SPH_FP64 with fixed_dt > 0 only (else
+ * SPH_ERR_INVALID_ARG).  Asynchronous. */
+int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *dalpha);
+
 /* Limits of sph_neighbour_list_static (points, cells of the grid). */
 #define SPH_STATIC_MAX_POINTS 524288
 #define SPH_STATIC_MAX_CELLS  16777216

@@ -1,0 +1,581 @@
+// Hand-written adjoint of one fixed-dt time step (PI + SU) and of the sensor
+// objective, SPH_FP64 form.
+//
+// Forward step n (Table 1 formulation; state x, v, u = v^{n-1}, rho,
+// sig = rho^{n-1}; F = fluid acceleration, D = density rate from PI):
+//   x' = x + dt v + dt^2/2 F      v' = u + 2dt F  (Euler step: v + dt F)
+//   u' = v                         rho' = sig + 2dt D (Euler: rho + dt D)
+//   sig' = rho                     boundary rho' clamped at rho0
+// Its adjoint, given the adjoint lam' of the state after the step:
+//   gF = dt^2/2 lam_x' + cv dt lam_v'        gD = cv dt lam_rho'   (cv = 2, Euler 1)
+//   lam_x = lam_x' + (PI terms)              lam_v = dt lam_x' + lam_u' [+ lam_v'] + (PI terms)
+//   lam_u = lam_v' [Euler: 0]                lam_rho = lam_sig' [+ lam_rho'] + (PI terms)
+//   lam_sig = lam_rho' [Euler: 0]
+// and the PI terms are the vector-Jacobian product of the pair sums with the
+// cotangents (gF, gD).  For an ordered pair a <- b, L = gF_a . f_ab + gD_a d_ab
+// depends on r_ab, v_ab, rho_a, rho_b and alpha; because the neighbour
+// relation is symmetric, every particle collects the derivatives of the
+// pairs it receives (a = self) and of the pairs it sources (b = self) by
+// walking its own 27 cells once: a gather, no atomics, deterministic.
+// dJ/dalpha is summed per block and the block sums are added in order.
+//
+// Arrays exchanged with the caller (lam, lam_next) are float64 in
+// persistent-id order with the layout of sph_get_state:
+//   [x: 3N][v: 3N][rho: N][v_prev: 3N][rho_prev: N]   (boundary x, v rows unused).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "sph_internal.cuh"
+
+namespace sph {
+
+namespace {
+
+constexpr int kAdjThreads = 128;
+
+struct PairGrad {
+    double rx, ry, rz;  // dL/dr_ab
+    double vx, vy, vz;  // dL/dv_ab
+    double rho_a, rho_b, alpha;
+};
+
+__device__ __forceinline__ double sound_of(const DevParams &P, double rho)
+{
+    double r = rho * P.inv_rho0;
+    return P.gamma_is_7 ? P.c0 * r * r * r : P.c0 * pow(r, 0.5 * (P.gamma - 1.0));
+}
+
+// Derivatives of L = gF . f_ab + gD d_ab for the ordered pair a <- b.
+//   f_ab = -m (P_a/rho_a^2 + P_b/rho_b^2 + Pi) F r     (when momentum)
+//   d_ab = m (v_ab . r) F,   grad_a W = F r
+__device__ __forceinline__ void pair_vjp(const DevParams &P, bool momentum, double rx, double ry,
+                                         double rz, double vx, double vy, double vz, double rho_a,
+                                         double rho_b, double P_a, double P_b, double c_a,
+                                         double c_b, double gFx, double gFy, double gFz,
+                                         double gD, PairGrad &g)
+{
+    const double m = P.mass;
+    double r2 = rx * rx + ry * ry + rz * rz;
+    double rl = sqrt(r2);
+    double q = rl * P.invh;
+    double F, dF;  // F(r) and dF/dr
+    if (q < 1.0) {
+        F = P.kA64 * (-3.0 + 2.25 * q);
+        dF = P.kA64 * 2.25 * P.invh;
+    } else {
+        double t = 2.0 - q;
+        F = P.kB64 * t * t / rl;
+        dF = P.kB64 * (-2.0 * t * P.invh / rl - t * t / r2);
+    }
+    double gx = dF * rx / rl, gy = dF * ry / rl, gz = dF * rz / rl;  // grad_r F
+    double vdr = vx * rx + vy * ry + vz * rz;
+    double den = r2 + P.eta2;
+    double mu = P.h * vdr / den;
+    // continuity
+    double cg = gD * m;
+    g.rx = cg * (F * vx + vdr * gx);
+    g.ry = cg * (F * vy + vdr * gy);
+    g.rz = cg * (F * vz + vdr * gz);
+    g.vx = cg * F * rx;
+    g.vy = cg * F * ry;
+    g.vz = cg * F * rz;
+    g.rho_a = 0.0;
+    g.rho_b = 0.0;
+    g.alpha = 0.0;
+    if (!momentum) return;
+    double sF = gFx * rx + gFy * ry + gFz * rz;
+    double S = rho_a + rho_b;
+    double K = 0.0, Pi = 0.0;
+    if (vdr < 0.0) {
+        K = -P.alpha * (c_a + c_b) / S;
+        Pi = K * mu;
+    }
+    double pr_a = P_a / (rho_a * rho_a), pr_b = P_b / (rho_b * rho_b);
+    double Q = pr_a + pr_b + Pi;
+    // L_m = -m Q F sF
+    double A = -m * Q * sF;   // times grad_r F
+    double Bc = -m * Q * F;   // times gF
+    double Cc = -m * F * sF;  // times dQ
+    // dPi/dr = K (h v / den - 2 h vdr r / den^2),  dPi/dv = K h r / den
+    double kv = K * P.h / den, kr = -2.0 * K * P.h * vdr / (den * den);
+    g.rx += A * gx + Bc * gFx + Cc * (kv * vx + kr * rx);
+    g.ry += A * gy + Bc * gFy + Cc * (kv * vy + kr * ry);
+    g.rz += A * gz + Bc * gFz + Cc * (kv * vz + kr * rz);
+    g.vx += Cc * kv * rx;
+    g.vy += Cc * kv * ry;
+    g.vz += Cc * kv * rz;
+    // d(P/rho^2)/drho = c^2/rho^2 - 2 P/rho^3;  dc/drho = c (gamma - 1) / (2 rho)
+    double dpr_a = c_a * c_a / (rho_a * rho_a) - 2.0 * P_a / (rho_a * rho_a * rho_a);
+    double dpr_b = c_b * c_b / (rho_b * rho_b) - 2.0 * P_b / (rho_b * rho_b * rho_b);
+    double dPi_a = 0.0, dPi_b = 0.0;
+    if (vdr < 0.0) {
+        double dca = c_a * (P.gamma - 1.0) / (2.0 * rho_a);
+        double dcb = c_b * (P.gamma - 1.0) / (2.0 * rho_b);
+        double cs = c_a + c_b;
+        dPi_a = -P.alpha * mu * (dca / S - cs / (S * S));
+        dPi_b = -P.alpha * mu * (dcb / S - cs / (S * S));
+        g.alpha = Cc * (-cs * mu / S);
+    }
+    g.rho_a = Cc * (dpr_a + dPi_a);
+    g.rho_b = Cc * (dpr_b + dPi_b);
+}
+
+__device__ __forceinline__ void cell_coords(const DevParams &P, uint32_t c, int *cx, int *cy,
+                                            int *cz)
+{
+    uint32_t t = c / (uint32_t)P.nx;
+    *cx = (int)(c - t * (uint32_t)P.nx);
+    *cy = (int)(t % (uint32_t)P.ny);
+    *cz = (int)(t / (uint32_t)P.ny);
+}
+
+// Visit the candidates j of the 9 x-runs of a list around cell (cx, cy, cz).
+#define FOR_RUNS(P, cx, cy, cz, start, j, ...)                                    \
+    {                                                                              \
+        int x0_ = max((cx) - 1, 0), x1_ = min((cx) + 1, (P).nx - 1);               \
+        for (int dz_ = -1; dz_ <= 1; ++dz_) {                                      \
+            int z_ = (cz) + dz_;                                                   \
+            if (z_ < 0 || z_ >= (P).nz) continue;                                  \
+            for (int dy_ = -1; dy_ <= 1; ++dy_) {                                  \
+                int y_ = (cy) + dy_;                                               \
+                if (y_ < 0 || y_ >= (P).ny) continue;                              \
+                int row_ = (P).nx * (y_ + (P).ny * z_);                            \
+                int e_ = (start)[row_ + x1_ + 1];                                  \
+                for (int j = (start)[row_ + x0_]; j < e_; ++j) { __VA_ARGS__ }     \
+            }                                                                      \
+        }                                                                          \
+    }
+
+// ---- adjoint SU ------------------------------------------------------------
+
+__global__ void k_adj_su_fluid(int nf, size_t N, DevParams P, const int32_t *__restrict__ fstart,
+                               const uint32_t *__restrict__ id,
+                               const double *__restrict__ lam_next, double *__restrict__ lam_s,
+                               double *__restrict__ gF, double *__restrict__ gD,
+                               const Scalars *__restrict__ sc)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    const bool euler = ((sc->step + 1) % P.euler_every) == 0;
+    const double dt = P.fixed_dt;
+    const size_t k = id[i];
+    const double *lx = lam_next + 3 * k, *lv = lam_next + 3 * N + 3 * k,
+                 *lu = lam_next + 7 * N + 3 * k;
+    const double lr = lam_next[6 * N + k], ls = lam_next[10 * N + k];
+    double *ox = lam_s + 3 * (size_t)i, *ov = lam_s + 3 * N + 3 * (size_t)i,
+           *ou = lam_s + 7 * N + 3 * (size_t)i;
+    if (i < fstart[P.ncells]) {
+        const double cv = euler ? 1.0 : 2.0;
+        for (int d = 0; d < 3; ++d) {
+            gF[3 * (size_t)i + d] = 0.5 * dt * dt * lx[d] + cv * dt * lv[d];
+            ox[d] = lx[d];
+            ov[d] = dt * lx[d] + lu[d] + (euler ? lv[d] : 0.0);
+            ou[d] = euler ? 0.0 : lv[d];
+        }
+        gD[i] = cv * dt * lr;
+        lam_s[6 * N + i] = ls + (euler ? lr : 0.0);
+        lam_s[10 * N + i] = euler ? 0.0 : lr;
+    } else {  // outside the grid: the forward step left the particle unchanged
+        for (int d = 0; d < 3; ++d) {
+            gF[3 * (size_t)i + d] = 0.0;
+            ox[d] = lx[d];
+            ov[d] = lv[d];
+            ou[d] = lu[d];
+        }
+        gD[i] = 0.0;
+        lam_s[6 * N + i] = lr;
+        lam_s[10 * N + i] = ls;
+    }
+}
+
+__global__ void k_adj_su_boundary(int nf, int nb, size_t N, DevParams P,
+                                  const int32_t *__restrict__ bstart,
+                                  const uint32_t *__restrict__ bid,
+                                  const double *__restrict__ brho, const double *__restrict__ brhom,
+                                  const double *__restrict__ bar,
+                                  const double *__restrict__ lam_next, double *__restrict__ lam_s,
+                                  double *__restrict__ gD, const Scalars *__restrict__ sc)
+{
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb) return;
+    const bool euler = ((sc->step + 1) % P.euler_every) == 0;
+    const double sdt = P.fixed_dt;
+    const size_t k = bid[j];
+    const size_t s = (size_t)nf + j;
+    const double lr = lam_next[6 * N + k], ls = lam_next[10 * N + k];
+    for (int d = 0; d < 3; ++d) {
+        lam_s[3 * s + d] = 0.0;
+        lam_s[3 * N + 3 * s + d] = 0.0;
+        lam_s[7 * N + 3 * s + d] = 0.0;
+    }
+    if (j < bstart[P.ncells]) {
+        // the forward density update, evaluated as in the forward kernel, decides the clamp
+        const double dtr = sdt;
+        double r = brho[j];
+        double nr = euler ? r + dtr * bar[j] : brhom[j] + (2.0 * sdt) * bar[j];
+        const double mask = (P.clamp && nr < P.rho0) ? 0.0 : 1.0;
+        const double cv = euler ? 1.0 : 2.0;
+        gD[s] = cv * sdt * mask * lr;
+        lam_s[6 * N + s] = ls + (euler ? mask * lr : 0.0);
+        lam_s[10 * N + s] = euler ? 0.0 : mask * lr;
+    } else {
+        gD[s] = 0.0;
+        lam_s[6 * N + s] = lr;
+        lam_s[10 * N + s] = ls;
+    }
+}
+
+// ---- adjoint PI --------------------------------------------------------------
+
+__global__ void __launch_bounds__(kAdjThreads)
+k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ posp,
+               const double4_32a *__restrict__ velr, const uint32_t *__restrict__ cell,
+               const int32_t *__restrict__ fstart, const double4_32a *__restrict__ bposp,
+               const double4_32a *__restrict__ bvelr, const int32_t *__restrict__ bstart,
+               const double *__restrict__ gF, const double *__restrict__ gD,
+               double *__restrict__ lam_s, double *__restrict__ part)
+{
+    __shared__ double red[kAdjThreads / 32];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    double dal = 0.0;
+    if (i < fstart[P.ncells]) {
+        const double4_32a pa = posp[i], va = velr[i];
+        const double rho_a = va.w, P_a = pa.w * rho_a * rho_a, c_a = sound_of(P, rho_a);
+        const double gFx = gF[3 * (size_t)i], gFy = gF[3 * (size_t)i + 1],
+                     gFz = gF[3 * (size_t)i + 2], gDa = gD[i];
+        double lx = 0, ly = 0, lz = 0, lvx = 0, lvy = 0, lvz = 0, lr = 0;
+        const double s2 = 4.0 * P.h * P.h;
+        int cx, cy, cz;
+        cell_coords(P, cell[i], &cx, &cy, &cz);
+        PairGrad g;
+        // fluid neighbours: F-F in both directions
+        FOR_RUNS(P, cx, cy, cz, fstart, j, {
+            if (j == i) continue;
+            const double4_32a pb = posp[j];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < s2)) continue;
+            const double4_32a vb = velr[j];
+            const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+            const double vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+            // self receives from j
+            pair_vjp(P, true, rx, ry, rz, vx, vy, vz, rho_a, rho_b, P_a, P_b, c_a, c_b, gFx, gFy,
+                     gFz, gDa, g);
+            lx += g.rx; ly += g.ry; lz += g.rz;
+            lvx += g.vx; lvy += g.vy; lvz += g.vz;
+            lr += g.rho_a;
+            dal += g.alpha;
+            // j receives from self (r_ji = -r, v_ji = -v)
+            pair_vjp(P, true, -rx, -ry, -rz, -vx, -vy, -vz, rho_b, rho_a, P_b, P_a, c_b, c_a,
+                     gF[3 * (size_t)j], gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gD[j], g);
+            lx -= g.rx; ly -= g.ry; lz -= g.rz;
+            lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
+            lr += g.rho_b;
+        })
+        // boundary neighbours: F-B (momentum + continuity) and B-F (continuity)
+        FOR_RUNS(P, cx, cy, cz, bstart, j, {
+            const double4_32a pb = bposp[j];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            if (!(r2 < s2)) continue;
+            const double4_32a vb = bvelr[j];
+            const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+            const double vx = va.x, vy = va.y, vz = va.z;
+            pair_vjp(P, true, rx, ry, rz, vx, vy, vz, rho_a, rho_b, P_a, P_b, c_a, c_b, gFx, gFy,
+                     gFz, gDa, g);
+            lx += g.rx; ly += g.ry; lz += g.rz;
+            lvx += g.vx; lvy += g.vy; lvz += g.vz;
+            lr += g.rho_a;
+            dal += g.alpha;
+            pair_vjp(P, false, -rx, -ry, -rz, -vx, -vy, -vz, rho_b, rho_a, P_b, P_a, c_b, c_a, 0.0,
+                     0.0, 0.0, gD[(size_t)nf + j], g);
+            lx -= g.rx; ly -= g.ry; lz -= g.rz;
+            lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
+        })
+        double *ox = lam_s + 3 * (size_t)i, *ov = lam_s + 3 * N + 3 * (size_t)i;
+        ox[0] += lx; ox[1] += ly; ox[2] += lz;
+        ov[0] += lvx; ov[1] += lvy; ov[2] += lvz;
+        lam_s[6 * N + i] += lr;
+    }
+    // deterministic block sum of dJ/dalpha
+    for (int o = 16; o > 0; o >>= 1) dal += __shfl_xor_sync(0xffffffffu, dal, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = dal;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) s += red[w];
+        part[blockIdx.x] = s;
+    }
+}
+
+// boundary particle j: the F-B pairs it sources give it a density adjoint
+__global__ void __launch_bounds__(kAdjThreads)
+k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__restrict__ bposp,
+                  const double4_32a *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
+                  const int32_t *__restrict__ bstart, const double4_32a *__restrict__ posp,
+                  const double4_32a *__restrict__ velr, const int32_t *__restrict__ fstart,
+                  const double *__restrict__ gF, const double *__restrict__ gD,
+                  double *__restrict__ lam_s)
+{
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= nb || j >= bstart[P.ncells]) return;
+    const double4_32a pb = bposp[j], vb = bvelr[j];
+    const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+    const double s2 = 4.0 * P.h * P.h;
+    int cx, cy, cz;
+    cell_coords(P, bcell[j], &cx, &cy, &cz);
+    double lr = 0.0;
+    PairGrad g;
+    FOR_RUNS(P, cx, cy, cz, fstart, i, {
+        const double4_32a pa = posp[i];
+        const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        if (!(r2 < s2)) continue;
+        const double4_32a va = velr[i];
+        const double rho_a = va.w, P_a = pa.w * rho_a * rho_a, c_a = sound_of(P, rho_a);
+        pair_vjp(P, true, rx, ry, rz, va.x, va.y, va.z, rho_a, rho_b, P_a, P_b, c_a, c_b,
+                 gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2], gD[i], g);
+        lr += g.rho_b;
+    })
+    lam_s[6 * N + (size_t)nf + j] += lr;
+}
+
+// sorted-order adjoint -> persistent-id order
+__global__ void k_adj_out(int nf, int nb, size_t N, const uint32_t *__restrict__ id,
+                          const uint32_t *__restrict__ bid, const double *__restrict__ lam_s,
+                          double *__restrict__ lam)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf + nb) return;
+    size_t k = i < nf ? id[i] : bid[i - nf];
+    for (int d = 0; d < 3; ++d) {
+        lam[3 * k + d] = lam_s[3 * (size_t)i + d];
+        lam[3 * N + 3 * k + d] = lam_s[3 * N + 3 * (size_t)i + d];
+        lam[7 * N + 3 * k + d] = lam_s[7 * N + 3 * (size_t)i + d];
+    }
+    lam[6 * N + k] = lam_s[6 * N + i];
+    lam[10 * N + k] = lam_s[10 * N + i];
+}
+
+__global__ void k_adj_alpha(const double *__restrict__ part, int n, double *dalpha)
+{
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += part[k];
+    *dalpha += s;
+}
+
+// ---- sensor objective ---------------------------------------------------------
+
+__device__ __forceinline__ double kernel_w(const DevParams &P, double r)
+{
+    double aD = P.kA64 * P.h * P.h;
+    double q = r * P.invh;
+    if (q < 1.0) return aD * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+    if (q < 2.0) {
+        double t = 2.0 - q;
+        return aD * 0.25 * t * t * t;
+    }
+    return 0.0;
+}
+
+__device__ __forceinline__ double pressure_of(const DevParams &P, double rho)
+{
+    double r = rho * P.inv_rho0;
+    double pw;
+    if (P.gamma_is_7) {
+        double r3 = r * r * r;
+        pw = r3 * r3 * r;
+    } else {
+        pw = pow(r, P.gamma);
+    }
+    return P.B * (pw - 1.0);
+}
+
+__device__ __forceinline__ int sensor_axis(double x, double mn, double inv_s, int n)
+{
+    double t = floor((x - mn) * inv_s);
+    if (!(t >= 0.0) || t >= (double)n) return -1;
+    return (int)t;
+}
+
+// One warp per sensor: Shepard sum over the fluid particles within 2h.
+template <typename Real>
+__global__ void k_sensor(int S, DevParams P, const double *__restrict__ spos,
+                         const double *__restrict__ x, const double *__restrict__ y,
+                         const double *__restrict__ z, const Real *__restrict__ rho,
+                         const int32_t *__restrict__ fstart, double *__restrict__ p_out,
+                         double *__restrict__ den_out)
+{
+    const int s = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;
+    const double xs = spos[3 * s], ys = spos[3 * s + 1], zs = spos[3 * s + 2];
+    int cx = sensor_axis(xs, P.dom_min[0], P.inv_s, P.nx);
+    int cy = sensor_axis(ys, P.dom_min[1], P.inv_s, P.ny);
+    int cz = sensor_axis(zs, P.dom_min[2], P.inv_s, P.nz);
+    double num = 0.0, den = 0.0;
+    if (cx >= 0 && cy >= 0 && cz >= 0) {
+        const double s2 = 4.0 * P.h * P.h;
+        int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
+        for (int dz = -1; dz <= 1; ++dz) {
+            int zz = cz + dz;
+            if (zz < 0 || zz >= P.nz) continue;
+            for (int dy = -1; dy <= 1; ++dy) {
+                int yy = cy + dy;
+                if (yy < 0 || yy >= P.ny) continue;
+                int row = P.nx * (yy + P.ny * zz);
+                int e = fstart[row + x1 + 1];
+                for (int b = fstart[row + x0] + lane; b < e; b += 32) {
+                    double dx = xs - x[b], dy2 = ys - y[b], dz2 = zs - z[b];
+                    double r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
+                    if (r2 < s2) {
+                        double rb = (double)rho[b];
+                        double w = kernel_w(P, sqrt(r2)) * P.mass / rb;
+                        num += w * pressure_of(P, rb);
+                        den += w;
+                    }
+                }
+            }
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        num += __shfl_xor_sync(0xffffffffu, num, o);
+        den += __shfl_xor_sync(0xffffffffu, den, o);
+    }
+    if (lane == 0) {
+        p_out[s] = den > 0.0 ? num / den : 0.0;
+        if (den_out) den_out[s] = den;
+    }
+}
+
+// dJ/d(x_b, rho_b) of J = sum_s g_s P_s, added into lam (id order), one thread
+// per fluid particle (the sensor set is small):
+//   dP_s/drho_b = (w_sb c_b^2 - (P_b - P_s) w_sb / rho_b) / den_s
+//   dP_s/dx_b   = (P_b - P_s) (m / rho_b) F(r_sb) (x_b - x_s) / den_s
+__global__ void k_sensor_adj(int nf, size_t N, int S, DevParams P, const double *__restrict__ spos,
+                             const double *__restrict__ g, const double *__restrict__ ps,
+                             const double *__restrict__ dens, const double *__restrict__ x,
+                             const double *__restrict__ y, const double *__restrict__ z,
+                             const double *__restrict__ rho, const uint32_t *__restrict__ id,
+                             const int32_t *__restrict__ fstart, double *__restrict__ lam)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf || i >= fstart[P.ncells]) return;
+    const double xi = x[i], yi = y[i], zi = z[i], rb = rho[i];
+    const double Pb = pressure_of(P, rb), cb = sound_of(P, rb);
+    const double s2 = 4.0 * P.h * P.h;
+    double lx = 0, ly = 0, lz = 0, lr = 0;
+    for (int s = 0; s < S; ++s) {
+        double dx = xi - spos[3 * s], dy = yi - spos[3 * s + 1], dz = zi - spos[3 * s + 2];
+        double r2 = dx * dx + dy * dy + dz * dz;
+        if (!(r2 < s2) || !(dens[s] > 0.0)) continue;
+        double r = sqrt(r2);
+        double w = kernel_w(P, r) * P.mass / rb;
+        double coef = g[s] / dens[s];
+        double dPs = Pb - ps[s];
+        lr += coef * (w * cb * cb - dPs * w / rb);
+        double q = r * P.invh;
+        double F = q < 1.0 ? P.kA64 * (-3.0 + 2.25 * q)
+                           : P.kB64 * (2.0 - q) * (2.0 - q) / r;
+        double f = coef * dPs * (P.mass / rb) * F;
+        lx += f * dx;
+        ly += f * dy;
+        lz += f * dz;
+    }
+    const size_t k = id[i];
+    lam[3 * k] += lx;
+    lam[3 * k + 1] += ly;
+    lam[3 * k + 2] += lz;
+    lam[6 * N + k] += lr;
+}
+
+template <typename Real>
+int sensor_launch(sph_ctx *ctx, const double *spos, int S, double *p_out, double *den_out)
+{
+    Workspace &w = ctx->w;
+    const int c = ctx->cur;
+    const int T = 128;
+    SPH_LAUNCH(ctx, k_sensor<Real>, (S * 32 + T - 1) / T, T, 0, ctx->stream, S, ctx->dp, spos,
+               w.x[c], w.y[c], w.z[c], (const Real *)w.rho[c], w.fstart, p_out, den_out);
+    return check_cuda(cudaGetLastError());
+}
+
+}  // namespace
+
+}  // namespace sph
+
+using namespace sph;
+
+extern "C" int sph_sensor_pressure(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
+                                   double *pressure)
+{
+    if (!ctx || n_sensors < 0 || (n_sensors > 0 && (!sensors || !pressure)))
+        return SPH_ERR_INVALID_ARG;
+    if (n_sensors > kMaxSensors) return SPH_ERR_TOO_LARGE;
+    if (!ctx->nl_valid) return SPH_ERR_SEQUENCE;
+    if (n_sensors == 0) return SPH_OK;
+    if (ctx->precision == SPH_FP32_SPLIT)
+        return sensor_launch<float>(ctx, sensors, (int)n_sensors, pressure, nullptr);
+    return sensor_launch<double>(ctx, sensors, (int)n_sensors, pressure, nullptr);
+}
+
+extern "C" int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
+                                  const double *dj_dp, double *lam)
+{
+    if (!ctx || n_sensors < 0 || (n_sensors > 0 && (!sensors || !dj_dp || !lam)))
+        return SPH_ERR_INVALID_ARG;
+    if (ctx->precision != SPH_FP64) return SPH_ERR_INVALID_ARG;
+    if (n_sensors > kMaxSensors) return SPH_ERR_TOO_LARGE;
+    if (!ctx->nl_valid) return SPH_ERR_SEQUENCE;
+    if (n_sensors == 0 || ctx->nf == 0) return SPH_OK;
+    Workspace &w = ctx->w;
+    int rc = sensor_launch<double>(ctx, sensors, (int)n_sensors, w.sens_p, w.sens_den);
+    if (rc) return rc;
+    const int c = ctx->cur, nf = (int)ctx->nf;
+    const size_t N = (size_t)(ctx->nf + ctx->nb);
+    const int T = 128;
+    SPH_LAUNCH(ctx, k_sensor_adj, (nf + T - 1) / T, T, 0, ctx->stream, nf, N, (int)n_sensors,
+               ctx->dp, sensors, dj_dp, w.sens_p, w.sens_den, w.x[c], w.y[c], w.z[c],
+               (const double *)w.rho[c], w.id[c], w.fstart, lam);
+    return check_cuda(cudaGetLastError());
+}
+
+extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *dalpha)
+{
+    if (!ctx || !lam_next || !lam || !dalpha || lam_next == lam) return SPH_ERR_INVALID_ARG;
+    if (ctx->precision != SPH_FP64 || !(ctx->prm.fixed_dt > 0.0)) return SPH_ERR_INVALID_ARG;
+    // forward NL and PI of the loaded state: the neighbour lists, packed inputs
+    // and (for the boundary clamp) the density rates of this step
+    int rc = sph_neighbour_list(ctx);
+    if (!rc) rc = sph_interact(ctx);
+    if (rc) return rc;
+    Workspace &w = ctx->w;
+    cudaStream_t st = ctx->stream;
+    const int nf = (int)ctx->nf, nb = (int)ctx->nb, c = ctx->cur;
+    const size_t N = (size_t)(nf + nb);
+    const int T = kAdjThreads;
+    const int blocks_f = (nf + T - 1) / T;
+    if (nf > 0)
+        SPH_LAUNCH(ctx, k_adj_su_fluid, blocks_f, T, 0, st, nf, N, ctx->dp, w.fstart, w.id[c],
+                   lam_next, w.adj_lam, w.adj_gF, w.adj_gD, w.sc);
+    if (nb > 0)
+        SPH_LAUNCH(ctx, k_adj_su_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
+                   w.bstart, w.bid, (const double *)w.brho, (const double *)w.brhom,
+                   (const double *)w.bar, lam_next, w.adj_lam, w.adj_gD, w.sc);
+    if (nf > 0)
+        SPH_LAUNCH(ctx, k_adj_pi_fluid, blocks_f, T, 0, st, nf, N, ctx->dp,
+                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
+                   (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
+                   w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part);
+    if (nb > 0 && nf > 0)
+        SPH_LAUNCH(ctx, k_adj_pi_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
+                   (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
+                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, w.adj_gF,
+                   w.adj_gD, w.adj_lam);
+    if (N > 0)
+        SPH_LAUNCH(ctx, k_adj_out, (unsigned)((N + T - 1) / T), T, 0, st, nf, nb, N, w.id[c],
+                   w.bid, w.adj_lam, lam);
+    if (nf > 0) SPH_LAUNCH(ctx, k_adj_alpha, 1, 1, 0, st, w.adj_part, blocks_f, dalpha);
+    return check_cuda(cudaGetLastError());
+}

@@ -171,6 +171,14 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.radix_hist = b.take<uint32_t>((size_t)hist);
     int64_t scan_n = hist > (int64_t)*ncells + 2 ? hist : (int64_t)*ncells + 2;
     W.scan_part = b.take<uint32_t>(scan_partials(scan_n));
+    if (p.precision == SPH_FP64) {
+        W.adj_gF = b.take<double>(3 * (size_t)nf + 1);
+        W.adj_gD = b.take<double>((size_t)(nf + nb) + 1);
+        W.adj_lam = b.take<double>((size_t)11 * (size_t)(nf + nb) + 1);
+        W.adj_part = b.take<double>((size_t)(nf / 128 + 2));
+    }
+    W.sens_p = b.take<double>(kMaxSensors);
+    W.sens_den = b.take<double>(kMaxSensors);
     W.stage = b.take<double>((size_t)11 * (size_t)(nf + nb) + 1);
     W.sc = b.take<Scalars>(1);
     W.counts4 = b.take<unsigned long long>(4);

@@ -79,6 +79,10 @@ struct Workspace {
     int32_t *fstart, *bstart; // [ncells + 2]
     uint32_t *radix_hist;     // [256 * tiles]
     uint32_t *scan_part;      // scan partials
+    // adjoint scratch (SPH_FP64 contexts): cotangents of F and D, the adjoint
+    // in sorted order (11 doubles per particle), per-block dJ/dalpha
+    double *adj_gF, *adj_gD, *adj_lam, *adj_part;
+    double *sens_p, *sens_den;  // sensor pressures and Shepard denominators
     // host exchange staging: 11 doubles per particle
     double *stage;
     Scalars *sc;
@@ -145,6 +149,7 @@ int check_cuda(cudaError_t e);
 
 // generic helpers
 constexpr int kRadixTile = 2048;   // keys per radix-sort tile (nl.cu)
+constexpr int kMaxSensors = 4096;  // sensor points per objective call
 constexpr int kScanBlock = 1024;
 constexpr int kScanItems = 4;
 constexpr int kScanTile = kScanBlock * kScanItems;

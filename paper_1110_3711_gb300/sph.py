@@ -98,6 +98,9 @@ def lib():
                 "sph_save_state": ([vp, vp], i32),
                 "sph_load_state": ([vp, vp], i32),
                 "sph_neighbour_list_static": ([pp, i64, vp, vp, vp, vp, vp], i32),
+                "sph_sensor_pressure": ([vp, vp, i64, vp], i32),
+                "sph_sensor_adjoint": ([vp, vp, i64, vp, vp], i32),
+                "sph_adjoint_step": ([vp, vp, vp, vp], i32),
                 "sph_error_string": ([i32], C.c_char_p),
                 "sph_destroy": ([vp], None),
             }
@@ -115,7 +118,8 @@ def exported_symbols():
             "sph_update", "sph_run", "sph_get_state", "sph_set_state", "sph_get_time",
             "sph_status", "sph_get_neighbour_list", "sph_get_grid", "sph_get_forces",
             "sph_count_work", "sph_launch_count", "sph_checkpoint_bytes", "sph_save_state",
-            "sph_load_state", "sph_neighbour_list_static", "sph_error_string", "sph_destroy"]
+            "sph_load_state", "sph_neighbour_list_static", "sph_sensor_pressure",
+            "sph_sensor_adjoint", "sph_adjoint_step", "sph_error_string", "sph_destroy"]
 
 
 def _check(code, what):
@@ -265,6 +269,21 @@ def sph_save_state(ctx, dst):
 
 def sph_load_state(ctx, src):
     _check(lib().sph_load_state(ctx, _ptr(src)), "sph_load_state")
+
+
+def sph_sensor_pressure(ctx, sensors, n_sensors, out):
+    _check(lib().sph_sensor_pressure(ctx, _ptr(sensors), int(n_sensors), _ptr(out)),
+           "sph_sensor_pressure")
+
+
+def sph_sensor_adjoint(ctx, sensors, n_sensors, dj_dp, lam):
+    _check(lib().sph_sensor_adjoint(ctx, _ptr(sensors), int(n_sensors), _ptr(dj_dp), _ptr(lam)),
+           "sph_sensor_adjoint")
+
+
+def sph_adjoint_step(ctx, lam_next, lam, dalpha):
+    _check(lib().sph_adjoint_step(ctx, _ptr(lam_next), _ptr(lam), _ptr(dalpha)),
+           "sph_adjoint_step")
 
 
 STATIC_MAX_POINTS = 524288

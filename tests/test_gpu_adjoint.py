@@ -1,0 +1,125 @@
+"""The hand-written adjoint (sph_adjoint_step, sph_sensor_adjoint) behind the
+torch.autograd.Function, against the gradient oracle and finite differences.
+
+Case: the small dam break (180 fluid + 1,304 boundary particles, dp = 0.02 m),
+fixed dt = 2e-4 s, 45 steps (so the Euler step at step 39 is included),
+objective = mean pressure of 4 sensors on the wall behind the column over the
+last 10 states, seeded N(0, 0.05 m/s) initial velocity.  Bars: J within
+1e-12, gradients within 1e-8 of the oracle (both float64; the remaining
+difference is summation order); checkpoint interval changes nothing; central
+differences of the GPU forward within 5e-6: a small eps is needed because the
+viscosity switch is C0 (see the oracle's tests), and at eps = 1e-7 the FD
+quotient's round-off floor is about 1e-16 * J / (2 eps |dJ/dd|) ~ 1.3e-6.
+"""
+import numpy as np
+import pytest
+
+from sphcases import small_dam, wall_sensors, dam_break
+from tests.gpu_common import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+STEPS, DT, WINDOW = 45, 2e-4, 10
+
+
+@pytest.fixture(scope="module")
+def torch_mod():
+    return need_gpu()
+
+
+def _case():
+    c = small_dam(0.02)
+    return c, wall_sensors(c, wall="back", n_y=2, n_z=2, z_top=0.12)
+
+
+def _gpu_grad(torch, case, spos, k, vel0=None, alpha=0.1, steps=STEPS, window=WINDOW, dt=DT):
+    from paper_1110_3711_gb300.autograd import DamBreakRun, objective
+    run = DamBreakRun(case, steps, dt, window, spos, checkpoint_every=k)
+    v = case.vel[:case.n_f] if vel0 is None else vel0
+    v0 = torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True)
+    a = torch.tensor(alpha, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = objective(v0, a, run)
+    J.backward()
+    return float(J.detach()), v0.grad.cpu().numpy(), float(a.grad), run
+
+
+def _gpu_j(torch, case, spos, vel0, alpha, steps=STEPS, window=WINDOW, dt=DT):
+    from paper_1110_3711_gb300.autograd import DamBreakRun
+    run = DamBreakRun(case, steps, dt, window, spos, checkpoint_every=steps)
+    return float(run.forward(torch.tensor(vel0, dtype=torch.float64, device="cuda"), alpha))
+
+
+def test_adjoint_matches_oracle_gradient(torch_mod):
+    from oracle import grad as G
+    c, spos = _case()
+    Jo, gvo, gao = G.gradient(c, c.vel[:c.n_f], 0.1, STEPS, DT, WINDOW, spos)
+    Jg, gvg, gag, _ = _gpu_grad(torch_mod, c, spos, k=7)
+    assert Jg == pytest.approx(Jo, rel=1e-12)
+    assert np.abs(gvg - gvo).max() <= 1e-8 * np.abs(gvo).max()
+    assert gag == pytest.approx(gao, rel=1e-8)
+
+
+def test_checkpoint_interval_does_not_change_gradient(torch_mod):
+    c, spos = _case()
+    ref = _gpu_grad(torch_mod, c, spos, k=1)
+    for k in (4, STEPS):
+        got = _gpu_grad(torch_mod, c, spos, k=k)
+        assert got[0] == ref[0]
+        assert np.array_equal(got[1], ref[1])
+        assert got[2] == ref[2]
+
+
+def test_adjoint_matches_gpu_finite_differences(torch_mod):
+    c, spos = _case()
+    _, gv, ga, _ = _gpu_grad(torch_mod, c, spos, k=10)
+    v0 = c.vel[:c.n_f].copy()
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        d = rng.normal(size=v0.shape)
+        eps = 1e-7
+        fd = (_gpu_j(torch_mod, c, spos, v0 + eps * d, 0.1)
+              - _gpu_j(torch_mod, c, spos, v0 - eps * d, 0.1)) / (2 * eps)
+        an = float((gv * d).sum())
+        assert abs(fd - an) <= 5e-6 * abs(an)
+    eps = 1e-6
+    fd_a = (_gpu_j(torch_mod, c, spos, v0, 0.1 + eps) - _gpu_j(torch_mod, c, spos, v0, 0.1 - eps)) / (2 * eps)
+    assert fd_a == pytest.approx(ga, rel=5e-6)
+
+
+def test_adjoint_step_needs_fixed_dt_fp64(torch_mod):
+    torch = torch_mod
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    lam = torch.zeros(11 * c.n, dtype=torch.float64, device="cuda")
+    lam2 = torch.zeros_like(lam)
+    da = torch.zeros(1, dtype=torch.float64, device="cuda")
+    for prec in ("fp64", "fp32"):
+        sim = sph.Simulation.from_case(c, precision=prec)   # variable dt
+        with pytest.raises(sph.SphError):
+            sph.sph_adjoint_step(sim.ctx, lam, lam2, da)
+
+
+@pytest.mark.slow
+def test_adjoint_differentiable_configuration(torch_mod):
+    """dp = 0.01 dam break (80,400 fluid + 58,606 boundary), fixed dt = 1e-4 s,
+    400 steps, checkpoints every 20 steps, 64 sensors on the wall behind the
+    column, mean over the last 100 states.  Central differences along the
+    normalised gradient (no cancellation between components) and in alpha.
+    The C0 viscosity switch limits FD accuracy, hence the
+    per-check bars."""
+    torch = torch_mod
+    from paper_1110_3711_gb300.autograd import DamBreakRun
+    c = dam_break(0.01, vel_sigma=0.05, seed=0, fixed_dt=1e-4)
+    spos = wall_sensors(c, wall="back")
+    J, gv, ga, run = _gpu_grad(torch, c, spos, k=20, steps=400, window=100, dt=1e-4)
+    assert run.stats["checkpoint_bytes"] < 1e9
+    v0 = c.vel[:c.n_f].copy()
+    d = gv / np.linalg.norm(gv)
+    eps = 1e-4
+    fd = (_gpu_j(torch, c, spos, v0 + eps * d, 0.1, steps=400, window=100, dt=1e-4)
+          - _gpu_j(torch, c, spos, v0 - eps * d, 0.1, steps=400, window=100, dt=1e-4)) / (2 * eps)
+    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-3)
+    eps = 1e-5
+    fd_a = (_gpu_j(torch, c, spos, v0, 0.1 + eps, steps=400, window=100, dt=1e-4)
+            - _gpu_j(torch, c, spos, v0, 0.1 - eps, steps=400, window=100, dt=1e-4)) / (2 * eps)
+    assert fd_a == pytest.approx(ga, rel=1e-3)
