@@ -47,6 +47,7 @@ WORKLOADS = {
     "dam1m": dict(dp=0.005, label="3D dam break dp=0.005 m (643,200 fluid + 232,727 boundary)"),
     "dam5m": dict(dp=0.0025, label="3D dam break dp=0.0025 m (5,145,600 fluid + 927,529 boundary)"),
     "dam10k": dict(dp=0.02, label="3D dam break dp=0.02 m (9,900 fluid + 14,744 boundary)"),
+    "dam20m": dict(dp=0.0016, label="3D dam break dp=0.0016 m (19,541,500 fluid + 2,259,259 boundary)"),
 }
 
 

@@ -14,8 +14,9 @@
 //      with |x_b|^2 beside them;
 //   3. tests all candidates against all 32 targets in lockstep: the warp reads
 //      one candidate (a shared-memory broadcast) and each lane evaluates
-//      |x_b|^2 - 2 x_a.x_b < 4h^2 - |x_a|^2 (three FMAs and a compare, the same
-//      test as |x_a - x_b|^2 < 4h^2), collecting a hit bit per candidate;
+//      |x_b|^2 - 2 x_a.x_b - (4h^2 - |x_a|^2) (three FMAs and a subtraction; it
+//      is negative exactly when |x_a - x_b|^2 < 4h^2 up to float32 rounding)
+//      and shifts its sign bit into a hit mask;
 //   4. walks its own hit bits (about 112 real neighbours per lane, so lanes
 //      stay balanced) and evaluates the pair terms of the oracle (cubic-spline
 //      gradient, Tait pressure, artificial viscosity, continuity) from the
@@ -75,7 +76,7 @@ __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, flo
     float rinv = rsqrtf(fmaxf(r2, 1e-30f));
     float r = r2 * rinv;
     float q = r * P.invhf;
-    float t = fmaxf(2.0f - q, 0.0f);
+    float t = 2.0f - q;
     float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
     float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
     float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
@@ -218,16 +219,21 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
             for (int q = 0; q < nch; ++q) {
-                // four independent partial masks keep the 32 tests free of a
-                // serial dependency chain
-                uint32_t m4[4] = {0u, 0u, 0u, 0u};
+                // the sign of t - thr is the hit bit; it is shifted into two
+                // independent 16-candidate masks (candidate k lands at bit 15 - k
+                // of its half), which are joined and bit-reversed so that
+                // candidate k ends at bit k
+                uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-                for (int k = 0; k < 32; ++k) {
+                for (int k = 0; k < 16; ++k) {
                     const float4 a = S.A[q * 32 + k];
-                    const float t = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w)));
-                    m4[k & 3] |= (t < thr ? 1u : 0u) << k;
+                    const float4 b = S.A[q * 32 + 16 + k];
+                    const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - thr;
+                    const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - thr;
+                    lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+                    hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
                 }
-                S.M[q][lane] = (m4[0] | m4[1]) | (m4[2] | m4[3]);
+                S.M[q][lane] = __brev((lo << 16) | hi);
             }
             // ---- every lane walks its own hits (about 112 per lane in all)
             int q = 0;
