@@ -136,12 +136,20 @@ def dist_env():
 
 
 def max_over_ranks(torch, value, world):
+    """Largest value over the ranks (the slowest rank's time)."""
     if world <= 1:
         return value
     import torch.distributed as dist
-    t = torch.tensor([value], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_steps_per_s(world, steps, max_ms):
+    """Whole-job throughput of independent replicas: every rank's steps over
+    the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
 
 
 def barrier(world):
@@ -214,7 +222,7 @@ def run_form(torch, case, precision, steps, warmup, flush, world, clocks=False, 
     tot = max_over_ranks(torch, t["total_ms"], world)
     counts = (np.asarray(c0, np.float64) + np.asarray(c1, np.float64)) / 2
     pairs = counts[1] + counts[3]
-    sps = world * steps / (tot / 1e3)
+    sps = replica_steps_per_s(world, steps, tot)
     res = dict(steps_per_s=sps, ms_per_step=tot / steps,
                interactions_per_s=pairs * sps,
                stage_ms=dict(nl=t["nl_ms"] / steps, pi=t["pi_ms"] / steps, su=t["su_ms"] / steps),

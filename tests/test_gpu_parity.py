@@ -225,3 +225,27 @@ def test_invalid_arguments_rejected(torch_mod):
         sph.sph_interact(sim.ctx)   # PI before NL
     with pytest.raises(sph.SphError):
         sph.sph_create(p, c.n_f, c.n_b, c.pos, c.vel, c.rho, sim.workspace.data_ptr(), 16, None)
+
+
+def test_device_flags_from_host_injected_faults(torch_mod):
+    """Failure detection without a GPU fault: a NaN planted in a host-side input
+    density and an absurd gravity (dt below 1e-12 s) surface as status bits and
+    as SPH_ERR_DEVICE_FLAG from the next synchronising call."""
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    rho = c.rho.copy()
+    rho[17] = np.nan
+    c_nan = type(c)(**{**c.__dict__, "rho": rho})
+    for prec in ("fp64", "fp32"):
+        sim = make_sim(c_nan, prec)
+        with pytest.raises(sph.SphError) as e:
+            sim.step(want_dt=True)
+        assert e.value.code == -4
+        assert sim.status(clear=True) & sph.FLAG_NAN
+        assert sim.status() == 0
+    c_g = dam_break(0.02)
+    c_g.params.g = (0.0, 0.0, -1e30)
+    sim = make_sim(c_g, "fp32")
+    with pytest.raises(sph.SphError):
+        sim.step(want_dt=True)
+    assert sim.status() & sph.FLAG_DT_TOO_SMALL
