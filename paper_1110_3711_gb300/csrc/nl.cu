@@ -55,13 +55,17 @@ __global__ void k_hash(const double *__restrict__ x, const double *__restrict__ 
                        Scalars *sc)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    uint32_t c = cell_of(P, x[i], y[i], z[i]);
-    uint32_t k = id ? id[i] - id_base : (uint32_t)i;
-    key_by_id[k] = c;
-    val_by_id[k] = (uint32_t)i;
-    atomicAdd(&count[c], 1u);
-    if (c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
+    // lanes past the end take a key no particle has, so the warp stays whole
+    uint32_t c = i < n ? cell_of(P, x[i], y[i], z[i]) : 0xffffffffu;
+    if (i < n) {
+        uint32_t k = id ? id[i] - id_base : (uint32_t)i;
+        key_by_id[k] = c;
+        val_by_id[k] = (uint32_t)i;
+    }
+    // consecutive particles share a cell: one atomic per distinct cell of the warp
+    unsigned peers = __match_any_sync(0xffffffffu, c);
+    if (i < n && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c], (uint32_t)__popc(peers));
+    if (i < n && c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
 }
 
 // ------------------------------------------------------------- radix sort --

@@ -175,14 +175,18 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
         __syncwarp();
 
         Acc o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        for (int base = 0; base < K; base += CAP) {
-            const int np = min(CAP, K - base);
+        // Pass p stages candidates p, p + npass, p + 2 npass, ...: every pass
+        // samples the whole neighbourhood, so every lane finds about 1/npass of
+        // its neighbours in each pass and the hit walks stay balanced.
+        const int npass = (K + CAP - 1) / CAP;
+        for (int pass = 0; pass < npass; ++pass) {
+            const int np = (K - pass + npass - 1) / npass;
             const int nch = (np + 31) >> 5;
             // ---- stage the candidates of this pass
             int r = 0;
             for (int m = 0; m < nch; ++m) {
                 const int ls = lane + 32 * m;
-                const int s = base + ls;
+                const int s = ls < np ? pass + npass * ls : K;
                 float4 a, v;
                 float pr;
                 if (s < K) {
