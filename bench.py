@@ -198,9 +198,10 @@ def time_steps(torch, sim, steps, flush):
     return dict(total_ms=tot, nl_ms=nl, pi_ms=pi, su_ms=su)
 
 
-def run_form(torch, case, precision, steps, warmup, flush, world, clocks=False, rank=0, local=0):
+def run_form(torch, case, precision, steps, warmup, flush, world, clocks=False, rank=0, local=0,
+             pi_kernel="warp"):
     from paper_1110_3711_gb300.sph import Simulation
-    sim = Simulation.from_case(case, precision=precision)
+    sim = Simulation.from_case(case, precision=precision, pi_kernel=pi_kernel)
     for _ in range(warmup):
         sim.step()
     c0 = counts_now(sim)
@@ -387,6 +388,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-5m", action="store_true", help="skip the 5M-particle lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ablation-steps", type=int, default=100,
+                    help="steps for each of the paper-design PI kernels (0: skip)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -422,6 +425,19 @@ def main():
         del sim64
 
     extra = {}
+    if args.ablation_steps > 0:
+        # the paper's GPU design on the same workload (Section 4, Fig. 11): one
+        # thread per particle, ranges from CellBeginEnd or precomputed per cell
+        # thread per particle, ranges from CellBeginEnd or precomputed per cell;
+        # all three designs over the same steps from the initial state
+        abl = {"steps": args.ablation_steps}
+        for kname in ("warp", "thread", "thread_fastcells"):
+            s_a, r_a = run_form(torch, case, "fp32", args.ablation_steps, 3, flush, world,
+                                pi_kernel=kname)
+            del s_a
+            abl[kname] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
+                          "stage_ms": r_a["stage_ms"]}
+        extra["pi_kernel_ablation"] = abl
     if not args.no_5m and args.workload != "dam5m":
         case5 = dam_break(WORKLOADS["dam5m"]["dp"])
         s5, r5 = run_form(torch, case5, "fp32", 100, 5, flush, world)

@@ -53,6 +53,14 @@ extern "C" {
 #define SPH_FP32_SPLIT 1  /* PI in float32 on cell-relative float32 offsets; float64
                              position accumulation and time-step reduction */
 
+/* PI kernel designs of the split form (same arithmetic, different mapping) */
+#define SPH_PI_WARP              0  /* one warp per cell: lockstep candidate tests in
+                                       shared memory, per-lane hit walks (default) */
+#define SPH_PI_THREAD            1  /* the paper's design: one thread per particle, 27
+                                       cells from CellBeginEnd (Section 4.4, Fig. 11 top) */
+#define SPH_PI_THREAD_FASTCELLS  2  /* one thread per particle, 9 ranges per cell
+                                       precomputed after NL (Fig. 11 bottom) */
+
 /* return codes */
 #define SPH_OK                 0
 #define SPH_ERR_INVALID_ARG   -1
@@ -88,7 +96,8 @@ typedef struct sph_params {
     double fixed_dt;      /* > 0: constant time step; <= 0: variable */
     int64_t clamp_boundary_rho; /* 1: boundary density never drops below rho0 */
     int32_t precision;    /* SPH_FP64 or SPH_FP32_SPLIT */
-    int32_t reserved;     /* must be 0 */
+    int32_t pi_kernel;    /* SPH_PI_* (SPH_FP32_SPLIT only; SPH_FP64 always uses one
+                             thread per particle) */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;

@@ -34,7 +34,8 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
     if (!(p->h > 0) || !(p->cell_size >= 2.0 * p->h * (1.0 - 1e-12)) || !(p->rho0 > 0) ||
         !(p->gamma > 0) || !(p->c0 > 0) || !(p->mass > 0) || !(p->cfl > 0) ||
         !(p->alpha >= 0) || !(p->eta2_coef > 0) || p->verlet_euler_every < 1 ||
-        (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) || p->reserved != 0)
+        (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) ||
+        p->pi_kernel < SPH_PI_WARP || p->pi_kernel > SPH_PI_THREAD_FASTCELLS)
         return SPH_ERR_INVALID_ARG;
     uint64_t nc = 1;
     for (int d = 0; d < 3; ++d) {
@@ -165,6 +166,10 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.ctr = W.count ? W.count + *ncells + 2 : nullptr;
     W.items_f = b.take<uint32_t>(nf > 0 ? nf : 1);
     W.items_b = b.take<uint32_t>(nb > 0 ? nb : 1);
+    if (p.precision == SPH_FP32_SPLIT && p.pi_kernel == SPH_PI_THREAD_FASTCELLS) {
+        W.franges = b.take<int4>((size_t)*ncells * 9);
+        W.branges = b.take<int4>((size_t)*ncells * 9);
+    }
     W.fstart = b.take<int32_t>((size_t)*ncells + 2);
     W.bstart = b.take<int32_t>((size_t)*ncells + 2);
     int64_t hist = (int64_t)256 * radix_tiles(m > 0 ? m : 1);
@@ -322,6 +327,7 @@ int load_state(sph_ctx *ctx, const double *pos, const double *vel, const double 
     int rc = stage_in(ctx, pos, vel, rho, velm, rhom);
     if (rc) return rc;
     ctx->cur = 0;
+    ctx->branges_ready = false;
     if (ctx->precision == SPH_FP32_SPLIT) launch_scatter_in<float>(ctx, 0);
     else launch_scatter_in<double>(ctx, 0);
     rc = nl_boundary_build(ctx);

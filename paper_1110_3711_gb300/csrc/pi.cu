@@ -234,7 +234,8 @@ int pi_launch(sph_ctx *ctx)
     int nf = (int)ctx->nf, nb = (int)ctx->nb;
     const int T = 128;
     if (ctx->precision == SPH_FP32_SPLIT) {
-        return pi32_launch(ctx);
+        if (ctx->prm.pi_kernel == SPH_PI_WARP) return pi32_launch(ctx);
+        return pi32_thread_launch(ctx);
     } else {
         if (nf > 0)
             SPH_LAUNCH(ctx, k_pi_fluid64, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,

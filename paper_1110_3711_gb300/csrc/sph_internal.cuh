@@ -76,6 +76,7 @@ struct Workspace {
     uint32_t *count;          // [ncells + 2], then the work-item counters ctr
     uint32_t *ctr;            // [0] fluid items, [1] fluid next, [2] boundary next, [3] boundary items
     uint32_t *items_f, *items_b;  // PI work items: first target index of a (cell, 32-target chunk)
+    int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
     int32_t *fstart, *bstart; // [ncells + 2]
     uint32_t *radix_hist;     // [256 * tiles]
     uint32_t *scan_part;      // scan partials
@@ -107,6 +108,7 @@ struct sph_ctx {
     long long launches;
     int device;
     int pi_grid_f, pi_grid_b;   // persistent grid sizes of the FP32 PI kernels
+    bool branges_ready;         // boundary x-run table built for the current boundary list
 };
 
 namespace sph {
@@ -135,6 +137,7 @@ size_t scan_partials(int64_t n);
 // PI (pi.cu, pi32.cu)
 int pi_launch(sph_ctx *ctx);
 int pi32_launch(sph_ctx *ctx);
+int pi32_thread_launch(sph_ctx *ctx);
 int pi32_setup(sph_ctx *ctx);
 int boundary_items_launch(sph_ctx *ctx);
 int count_work_launch(sph_ctx *ctx);

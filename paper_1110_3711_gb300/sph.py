@@ -18,6 +18,7 @@ from . import build as _build
 
 SPH_FP64 = 0
 SPH_FP32_SPLIT = 1
+PI_KERNELS = {"warp": 0, "thread": 1, "thread_fastcells": 2}
 FLAG_OUT_OF_GRID = 1
 FLAG_NAN = 2
 FLAG_DT_TOO_SMALL = 4
@@ -40,10 +41,10 @@ class sph_params(C.Structure):
                 ("mass", C.c_double), ("g", C.c_double * 3), ("dom_min", C.c_double * 3),
                 ("dom_max", C.c_double * 3), ("verlet_euler_every", C.c_int64),
                 ("fixed_dt", C.c_double), ("clamp_boundary_rho", C.c_int64),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("pi_kernel", C.c_int32)]
 
 
-def make_params(run_params, precision) -> sph_params:
+def make_params(run_params, precision, pi_kernel="warp") -> sph_params:
     """Fill ``sph_params`` from any object with the same field names."""
     prec = {"fp64": SPH_FP64, "fp32": SPH_FP32_SPLIT, "fp32_split": SPH_FP32_SPLIT}.get(
         precision, precision)
@@ -58,7 +59,7 @@ def make_params(run_params, precision) -> sph_params:
     p.verlet_euler_every = int(run_params.verlet_euler_every)
     p.clamp_boundary_rho = int(run_params.clamp_boundary_rho)
     p.precision = int(prec)
-    p.reserved = 0
+    p.pi_kernel = int(PI_KERNELS.get(pi_kernel, pi_kernel))
     return p
 
 
@@ -311,11 +312,11 @@ class Simulation:
     runs in libsph."""
 
     def __init__(self, run_params, n_f, n_b, pos, vel, rho, precision="fp32", device=None,
-                 stream=None):
+                 stream=None, pi_kernel="warp"):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
-        self.params = make_params(run_params, precision)
+        self.params = make_params(run_params, precision, pi_kernel)
         self.n_f, self.n_b = int(n_f), int(n_b)
         self.n = self.n_f + self.n_b
         self.ws_bytes = sph_workspace_bytes(self.params, self.n_f, self.n_b)

@@ -13,6 +13,7 @@ def need_gpu():
 
 
 def make_sim(case, precision, **kw):
+    """Simulation of a case through the C ABI (kw: device, stream, pi_kernel)."""
     from paper_1110_3711_gb300.sph import Simulation
     return Simulation.from_case(case, precision=precision, **kw)
 

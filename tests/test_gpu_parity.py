@@ -115,13 +115,15 @@ def test_pi_fp64_matches_oracle(torch_mod, O, case_fn):
     assert mx[1] == pytest.approx(max(O.sound(c.params, r) for r in rho), rel=1e-13)
 
 
-def test_pi_fp32_split_matches_oracle(torch_mod, O):
-    """float32 PI on cell-relative offsets: errors relative to the force scale
-    (|g| + max|ace|) within 2e-5 and density rates within 2e-5 of their scale."""
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "thread_fastcells"])
+def test_pi_fp32_split_matches_oracle(torch_mod, O, pi_kernel):
+    """float32 PI on cell-relative offsets, every PI kernel design: errors
+    relative to the force scale (|g| + max|ace|) within 2e-5 and density rates
+    within 2e-5 of their scale."""
     c = dam_break(0.01)
     vel, rho = _random_state(c, 2)
     c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho})
-    sim = make_sim(c2, "fp32")
+    sim = make_sim(c2, "fp32", pi_kernel=pi_kernel)
     sim.neighbour_list()
     sim.interact()
     ace, ar, mx = sim.forces()
@@ -155,10 +157,11 @@ def test_fp64_time_loop_matches_oracle(torch_mod, O):
     assert nsteps == steps and tt == pytest.approx(t, rel=1e-12)
 
 
-def test_fp32_split_time_loop_error_budget(torch_mod, O):
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread_fastcells"])
+def test_fp32_split_time_loop_error_budget(torch_mod, O, pi_kernel):
     """SPH_FP32_SPLIT against the FP64 oracle after 100 steps."""
     c = dam_break(0.02)
-    sim = make_sim(c, "fp32")
+    sim = make_sim(c, "fp32", pi_kernel=pi_kernel)
     st = O.State(c)
     for _ in range(100):
         sim.step()
