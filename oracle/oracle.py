@@ -31,7 +31,8 @@ class OrParams(C.Structure):
                 ("mass", C.c_double), ("g", C.c_double * 3),
                 ("dom_min", C.c_double * 3), ("dom_max", C.c_double * 3),
                 ("verlet_euler_every", C.c_int64), ("fixed_dt", C.c_double),
-                ("clamp_boundary_rho", C.c_int64)]
+                ("clamp_boundary_rho", C.c_int64), ("tensile_eps", C.c_double),
+                ("tensile_pos", C.c_double), ("tensile_n", C.c_int64)]
 
 
 def build(force: bool = False) -> str:
@@ -98,6 +99,9 @@ def params(p) -> OrParams:
             arr[k] = float(v)
     o.verlet_euler_every = int(p.verlet_euler_every)
     o.clamp_boundary_rho = int(p.clamp_boundary_rho)
+    o.tensile_eps = float(getattr(p, "tensile_eps", 0.0))
+    o.tensile_pos = float(getattr(p, "tensile_pos", 0.0))
+    o.tensile_n = int(getattr(p, "tensile_n", 4))
     return o
 
 

@@ -43,6 +43,8 @@ typedef struct {
     int64_t verlet_euler_every;
     double fixed_dt;
     int64_t clamp_boundary_rho;
+    double tensile_eps, tensile_pos;
+    int64_t tensile_n;
 } or_params;
 
 #define OR_PI 3.14159265358979323846
@@ -153,10 +155,24 @@ double or_sound(const or_params *p, double rho)
  * with the artificial viscosity of Monaghan (1992; Table 1):
  *   mu_ab = h v_ab.r_ab / (r^2 + eta^2),  eta^2 = 0.01 h^2
  *   Pi_ab = -alpha cbar_ab mu_ab / rhobar_ab  if v_ab.r_ab < 0, else 0
- *   momentum:   dv_a/dt   += -m_b (P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab) grad_a W_ab
+ *   momentum:   dv_a/dt   += -m_b (P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab + T_ab) grad_a W_ab
  *   continuity: drho_a/dt += m_b v_ab . grad_a W_ab
- * and the viscous time-step term |h v_ab.r_ab / (r^2 + eta^2)|. */
+ * and the viscous time-step term |h v_ab.r_ab / (r^2 + eta^2)|.
+ * T_ab is the tensile correction of Monaghan (2000) (the "tensil" array of
+ * Table 3; zero unless tensile_eps or tensile_pos is set):
+ *   T_ab = R_ab (W(r_ab) / W(dp))^n,
+ *   R_ab = tensile_pos (P_a/rho_a^2 + P_b/rho_b^2)      if P_a > 0 and P_b > 0,
+ *        = R_a + R_b, R = tensile_eps |P|/rho^2 for P < 0 and 0 otherwise. */
 typedef struct { double acc[3], ar, visc; } pair_out;
+
+static double tensile_r(const or_params *p, double Pa, double rhoa, double Pb, double rhob)
+{
+    if (Pa > 0.0 && Pb > 0.0) return p->tensile_pos * (Pa / (rhoa * rhoa) + Pb / (rhob * rhob));
+    double R = 0.0;
+    if (Pa < 0.0) R += p->tensile_eps * fabs(Pa) / (rhoa * rhoa);
+    if (Pb < 0.0) R += p->tensile_eps * fabs(Pb) / (rhob * rhob);
+    return R;
+}
 
 static void pair_terms(const or_params *p, int momentum,
                        const double *xa, const double *va, double rhoa, double Pa, double ca,
@@ -177,9 +193,14 @@ static void pair_terms(const or_params *p, int momentum,
         double rhobar = 0.5 * (rhoa + rhob);
         Pi = -p->alpha * cbar * mu / rhobar;
     }
+    double T = 0.0;
+    if (p->tensile_eps != 0.0 || p->tensile_pos != 0.0) {
+        double f = or_kernel_w(p->h, r) / or_kernel_w(p->h, p->dp);
+        T = tensile_r(p, Pa, rhoa, Pb, rhob) * pow(f, (double)p->tensile_n);
+    }
     for (int d = 0; d < 3; ++d) o->acc[d] = 0.0;
     if (momentum) {
-        double coef = -p->mass * (Pa / (rhoa * rhoa) + Pb / (rhob * rhob) + Pi);
+        double coef = -p->mass * (Pa / (rhoa * rhoa) + Pb / (rhob * rhob) + Pi + T);
         for (int d = 0; d < 3; ++d) o->acc[d] = coef * (F * r_ab[d]);
     }
     o->ar = p->mass * (vdr * F);

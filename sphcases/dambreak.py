@@ -59,6 +59,9 @@ class RunParams:
     verlet_euler_every: int = 40
     fixed_dt: float = 0.0
     clamp_boundary_rho: int = 1
+    tensile_eps: float = 0.0     # tensile correction for negative pressures (0: off)
+    tensile_pos: float = 0.0     # ... for two positive pressures
+    tensile_n: int = 4           # exponent of W(r)/W(dp)
 
     def as_dict(self):
         return asdict(self)
