@@ -98,6 +98,15 @@ typedef struct sph_params {
     int32_t precision;    /* SPH_FP64 or SPH_FP32_SPLIT */
     int32_t pi_kernel;    /* SPH_PI_* (SPH_FP32_SPLIT only; SPH_FP64 always uses one
                              thread per particle) */
+    /* Tensile correction (Monaghan 2000; the "tensil" term of Table 3), off when
+     * both coefficients are 0: the momentum term P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab
+     * gains R_ab (W(r)/W(dp))^n with R_ab = tensile_pos (P_a/rho_a^2 + P_b/rho_b^2)
+     * if both pressures are positive, else the sum of tensile_eps |P|/rho^2 over
+     * the negative ones.  Supported by SPH_FP64 and by SPH_PI_WARP; not by the
+     * thread-per-particle kernels or the adjoint (SPH_ERR_INVALID_ARG). */
+    double tensile_eps;
+    double tensile_pos;
+    int64_t tensile_n;    /* exponent n >= 1 (4 in Monaghan 2000) */
 } sph_params;
 
 typedef struct sph_ctx sph_ctx;
@@ -222,8 +231,8 @@ int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
  * (left valid, so sph_sensor_adjoint may follow), then writes to lam the adjoint
  * of the state at the start of the step given lam_next, the adjoint of the state
  * after it, and adds dJ/dalpha to *dalpha.  lam, lam_next and dalpha are device
- * memory and must not alias.  SPH_FP64 with fixed_dt > 0 only (else
- * SPH_ERR_INVALID_ARG).  Asynchronous. */
+ * memory and must not alias.  SPH_FP64 with fixed_dt > 0 and no tensile
+ * correction only (else SPH_ERR_INVALID_ARG).  Asynchronous. */
 int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *dalpha);
 
 /* Limits of sph_neighbour_list_static (points, cells of the grid). */

@@ -544,7 +544,8 @@ extern "C" int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n
 extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *dalpha)
 {
     if (!ctx || !lam_next || !lam || !dalpha || lam_next == lam) return SPH_ERR_INVALID_ARG;
-    if (ctx->precision != SPH_FP64 || !(ctx->prm.fixed_dt > 0.0)) return SPH_ERR_INVALID_ARG;
+    if (ctx->precision != SPH_FP64 || !(ctx->prm.fixed_dt > 0.0) || ctx->dp.tensile)
+        return SPH_ERR_INVALID_ARG;
     // forward NL and PI of the loaded state: the neighbour lists, packed inputs
     // and (for the boundary clamp) the density rates of this step
     int rc = sph_neighbour_list(ctx);

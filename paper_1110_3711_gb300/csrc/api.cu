@@ -37,6 +37,10 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
         (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) ||
         p->pi_kernel < SPH_PI_WARP || p->pi_kernel > SPH_PI_THREAD_FASTCELLS)
         return SPH_ERR_INVALID_ARG;
+    const bool tensile = p->tensile_eps != 0.0 || p->tensile_pos != 0.0;
+    if (tensile && (p->tensile_n < 1 || p->tensile_n > 16 || !(p->dp > 0) ||
+                    (p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_WARP)))
+        return SPH_ERR_INVALID_ARG;
     uint64_t nc = 1;
     for (int d = 0; d < 3; ++d) {
         double span = p->dom_max[d] - p->dom_min[d];
@@ -97,6 +101,22 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
     d.sf = (float)p.cell_size;
     d.kA = (float)d.kA64;
     d.kB = (float)d.kB64;
+    d.aDf = (float)aD;
+    d.tensile = (p.tensile_eps != 0.0 || p.tensile_pos != 0.0) ? 1 : 0;
+    d.tensile_n = (int)p.tensile_n;
+    d.tens_eps = p.tensile_eps;
+    d.tens_pos = p.tensile_pos;
+    if (d.tensile) {
+        // W(dp) of the cubic spline (the reference spacing of the correction)
+        double q = p.dp / p.h, w;
+        if (q < 1.0) w = aD * (1.0 - 1.5 * q * q + 0.75 * q * q * q);
+        else if (q < 2.0) w = aD * 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+        else w = 0.0;
+        d.inv_wdp = w > 0.0 ? 1.0 / w : 0.0;
+    }
+    d.tens_epsf = (float)d.tens_eps;
+    d.tens_posf = (float)d.tens_pos;
+    d.inv_wdpf = (float)d.inv_wdp;
     return d;
 }
 

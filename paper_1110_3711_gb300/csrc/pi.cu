@@ -42,6 +42,21 @@ struct Acc64 {
     double ax, ay, az, ar, vis;
 };
 
+// Tensile correction of Monaghan (2000): R_ab (W(r)/W(dp))^n, with pr = P/rho^2
+// (same sign as P) of the two particles.
+__device__ __forceinline__ double tensile64(const DevParams &P, double q, double pra, double prb)
+{
+    double aD = P.kA64 * P.h * P.h;
+    double w = q < 1.0 ? aD * (1.0 - 1.5 * q * q + 0.75 * q * q * q)
+                       : aD * 0.25 * (2.0 - q) * (2.0 - q) * (2.0 - q);
+    double f = w * P.inv_wdp, fn = 1.0;
+    for (int k = 0; k < P.tensile_n; ++k) fn *= f;
+    double R = (pra > 0.0 && prb > 0.0)
+                   ? P.tens_pos * (pra + prb)
+                   : P.tens_eps * (fmax(-pra, 0.0) + fmax(-prb, 0.0));
+    return R * fn;
+}
+
 template <bool MOMENTUM>
 __device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa, const double4_32a &va,
                                        double ca, const double4_32a &pb, const double4_32a &vb, double rx,
@@ -61,6 +76,7 @@ __device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa
             double cb = P.gamma_is_7 ? P.c0 * rb * rb * rb : P.c0 * pow(rb, 0.5 * (P.gamma - 1.0));
             Pi = -P.alpha * (ca + cb) * mu / (va.w + vb.w);
         }
+        if (P.tensile) Pi += tensile64(P, q, pa.w, pb.w);
         double coef = -(pa.w + pb.w + Pi) * F;
         o.ax += coef * rx;
         o.ay += coef * ry;

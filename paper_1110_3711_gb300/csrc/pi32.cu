@@ -66,7 +66,19 @@ struct Acc {
 
 // Terms of one ordered pair a <- b (see the oracle): momentum sum, continuity
 // sum and the viscous dt term.
-template <bool MOMENTUM>
+// Tensile correction of Monaghan (2000): R_ab (W(r)/W(dp))^n (see the FP64 form).
+__device__ __forceinline__ float tensile32(const DevParams &P, float q, float pra, float prb)
+{
+    float t = 2.0f - q;
+    float w = q < 1.0f ? P.aDf * fmaf(q * q, fmaf(0.75f, q, -1.5f), 1.0f) : P.aDf * 0.25f * t * t * t;
+    float f = w * P.inv_wdpf, fn = 1.0f;
+    for (int k = 0; k < P.tensile_n; ++k) fn *= f;
+    float R = (pra > 0.0f && prb > 0.0f) ? P.tens_posf * (pra + prb)
+                                          : P.tens_epsf * (fmaxf(-pra, 0.0f) + fmaxf(-prb, 0.0f));
+    return R * fn;
+}
+
+template <bool MOMENTUM, bool TENSILE>
 __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, float za,
                                      const float4 &pa, const float4 &va, float ca,
                                      const float4 &b, const float4 &vb, float prb, Acc &o)
@@ -85,6 +97,7 @@ __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, flo
         float rb = vb.w * P.inv_rho0f;
         float cb = P.c0f * rb * rb * rb;
         float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
+        if (TENSILE) Pi += tensile32(P, q, pa.w, prb);
         float coef = -(pa.w + prb + Pi) * F;
         o.ax = fmaf(coef, rx, o.ax);
         o.ay = fmaf(coef, ry, o.ay);
@@ -96,7 +109,7 @@ __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, flo
 
 // MOMENTUM: fluid targets (F-F and F-B, acc out).  !MOMENTUM: boundary targets
 // (B-F continuity only, bar out).
-template <bool MOMENTUM>
+template <bool MOMENTUM, bool TENSILE>
 __global__ void __launch_bounds__(WARPS * 32, SPH_PI_MINB)
 k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restrict__ n_items_p,
        uint32_t *__restrict__ next_p, const float4 *__restrict__ tposp,
@@ -250,7 +263,7 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                 if (m == 0u) break;
                 const int ls = q * 32 + __ffs(m) - 1;
                 m &= m - 1u;
-                pair<MOMENTUM>(P, xa, ya, za, pa, va, ca, S.A[ls], S.V[ls], S.Pr[ls], o);
+                pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, ca, S.A[ls], S.V[ls], S.Pr[ls], o);
             }
             __syncwarp();
         }
@@ -307,9 +320,16 @@ int pi32_setup(sph_ctx *ctx)
     if (check_cuda(cudaGetDevice(&dev))) return SPH_ERR_CUDA;
     if (check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
         return SPH_ERR_CUDA;
-    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true>, WARPS * 32, 0)))
+    if (ctx->dp.tensile) {
+        if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true, true>,
+                                                                    WARPS * 32, 0)))
+            return SPH_ERR_CUDA;
+    } else if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true, false>,
+                                                                       WARPS * 32, 0))) {
         return SPH_ERR_CUDA;
-    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_pi32<false>, WARPS * 32, 0)))
+    }
+    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_pi32<false, false>,
+                                                                WARPS * 32, 0)))
         return SPH_ERR_CUDA;
     ctx->pi_grid_f = sms * (bf > 0 ? bf : 1);
     ctx->pi_grid_b = sms * (bb > 0 ? bb : 1);
@@ -333,14 +353,22 @@ int pi32_launch(sph_ctx *ctx)
     cudaStream_t st = ctx->stream;
     // clear the two "next item" counters (fluid, boundary)
     if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, 2 * sizeof(uint32_t), st))) return SPH_ERR_CUDA;
-    if (ctx->nf > 0)
-        SPH_LAUNCH(ctx, k_pi32<true>, ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp, w.items_f,
-                   &w.ctr[0], &w.ctr[1], (const float4 *)w.posp, (const float4 *)w.velr, w.cell,
-                   w.fstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
-                   (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc,
-                   (float *)nullptr, w.sc);
+    if (ctx->nf > 0) {
+        if (ctx->dp.tensile)
+            SPH_LAUNCH(ctx, (k_pi32<true, true>), ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp,
+                       w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
+                       (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
+                       (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
+                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr, w.sc);
+        else
+            SPH_LAUNCH(ctx, (k_pi32<true, false>), ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp,
+                       w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
+                       (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
+                       (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
+                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr, w.sc);
+    }
     if (ctx->nb > 0)
-        SPH_LAUNCH(ctx, k_pi32<false>, ctx->pi_grid_b, WARPS * 32, 0, st, ctx->dp, w.items_b,
+        SPH_LAUNCH(ctx, (k_pi32<false, false>), ctx->pi_grid_b, WARPS * 32, 0, st, ctx->dp, w.items_b,
                    &w.ctr[3], &w.ctr[2], (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell,
                    w.bstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
                    (const float4 *)nullptr, (const float4 *)nullptr, w.bstart, (float4 *)nullptr,

@@ -49,9 +49,13 @@ struct DevParams {
     int euler_every;
     int clamp;
     int gamma_is_7;
+    int tensile;          // tensile correction on
+    int tensile_n;
+    double tens_eps, tens_pos, inv_wdp;   // inv_wdp = 1 / W(dp)
     // float copies for the FP32 path
     float hf, invhf, four_h2f, eta2f, massf, alphaf, c0f, inv_rho0f, Bf, sf;
     float kA, kB;   // grad-W factor constants (see pi.cu)
+    float aDf, tens_epsf, tens_posf, inv_wdpf;  // 1/(pi h^3) and the tensile constants
     float gf[3];
 };
 

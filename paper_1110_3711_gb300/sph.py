@@ -41,7 +41,9 @@ class sph_params(C.Structure):
                 ("mass", C.c_double), ("g", C.c_double * 3), ("dom_min", C.c_double * 3),
                 ("dom_max", C.c_double * 3), ("verlet_euler_every", C.c_int64),
                 ("fixed_dt", C.c_double), ("clamp_boundary_rho", C.c_int64),
-                ("precision", C.c_int32), ("pi_kernel", C.c_int32)]
+                ("precision", C.c_int32), ("pi_kernel", C.c_int32),
+                ("tensile_eps", C.c_double), ("tensile_pos", C.c_double),
+                ("tensile_n", C.c_int64)]
 
 
 def make_params(run_params, precision, pi_kernel="warp") -> sph_params:
@@ -60,6 +62,9 @@ def make_params(run_params, precision, pi_kernel="warp") -> sph_params:
     p.clamp_boundary_rho = int(run_params.clamp_boundary_rho)
     p.precision = int(prec)
     p.pi_kernel = int(PI_KERNELS.get(pi_kernel, pi_kernel))
+    p.tensile_eps = float(getattr(run_params, "tensile_eps", 0.0))
+    p.tensile_pos = float(getattr(run_params, "tensile_pos", 0.0))
+    p.tensile_n = int(getattr(run_params, "tensile_n", 4))
     return p
 
 

@@ -252,3 +252,49 @@ def test_device_flags_from_host_injected_faults(torch_mod):
     with pytest.raises(sph.SphError):
         sim.step(want_dt=True)
     assert sim.status() & sph.FLAG_DT_TOO_SMALL
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_pi_tensile_correction_matches_oracle(torch_mod, O, precision, tol):
+    """The tensile-correction variant (Monaghan 2000; Table 3's tensil term)
+    with eps = 0.2, 0.01 for positive pressures, n = 4, and alpha = 0.25 as in
+    Table 1, on a state with both signs of pressure."""
+    import copy
+    c = dam_break(0.02)
+    rng = np.random.default_rng(11)
+    vel, rho = _random_state(c, 3)
+    rho = rho * (1 + rng.normal(0, 4e-3, size=c.n))
+    p = copy.copy(c.params)
+    p.alpha, p.tensile_eps, p.tensile_pos, p.tensile_n = 0.25, 0.2, 0.01, 4
+    c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho, "params": p})
+    sim = make_sim(c2, precision)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, _ = sim.forces()
+    oace, oar, _, _, _ = O.interact(p, c.n_f, c.n_b, c.pos, vel, rho)
+    ref = copy.copy(p)
+    ref.tensile_eps = ref.tensile_pos = 0.0
+    base, _, _, _, _ = O.interact(ref, c.n_f, c.n_b, c.pos, vel, rho)
+    assert np.abs(oace - base).max() > 1e-3 * np.abs(base).max()   # the term matters here
+    scale = np.abs(oace).max() + (9.81 if precision == "fp32" else 0.0)
+    assert np.abs(ace - oace).max() <= tol * scale
+    assert np.abs(ar - oar).max() <= tol * np.abs(oar).max()
+
+
+def test_tensile_rejected_where_unsupported(torch_mod):
+    import copy
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    p = copy.copy(c.params)
+    p.tensile_eps = 0.2
+    for prec, kern in (("fp32", "thread"), ("fp32", "thread_fastcells")):
+        with pytest.raises(sph.SphError):
+            sph.sph_workspace_bytes(sph.make_params(p, prec, kern), c.n_f, c.n_b)
+    p.fixed_dt = 1e-4
+    c2 = type(c)(**{**c.__dict__, "params": p})
+    sim = make_sim(c2, "fp64")
+    torch = torch_mod
+    lam = torch.zeros(11 * c.n, dtype=torch.float64, device="cuda")
+    with pytest.raises(sph.SphError):
+        sph.sph_adjoint_step(sim.ctx, lam, torch.zeros_like(lam),
+                             torch.zeros(1, dtype=torch.float64, device="cuda"))
