@@ -146,6 +146,15 @@ int sph_update(sph_ctx *ctx, double *dt_out);
 /* n_steps repetitions of NL, PI, SU.  Asynchronous. */
 int sph_run(sph_ctx *ctx, int64_t n_steps);
 
+/* The same steps replayed from a CUDA graph: two consecutive steps (the
+ * particle buffers swap every step, so that pair repeats) are captured once
+ * per context and launched n_steps / 2 times, an odd last step runs as
+ * ordinary launches.  Results are identical to sph_run.  Needs a stream created
+ * by the caller (not the legacy or per-thread default stream; else
+ * SPH_ERR_INVALID_ARG).  The executable graphs are driver resources released by
+ * sph_destroy.  Asynchronous. */
+int sph_run_graph(sph_ctx *ctx, int64_t n_steps);
+
 /* Copy the state out in persistent-id order (any pointer may be NULL).
  * vel_prev / rho_prev are the previous Verlet level.  Synchronises. */
 int sph_get_state(sph_ctx *ctx, double *pos, double *vel, double *rho,

@@ -472,6 +472,48 @@ int sph_run(sph_ctx *ctx, int64_t n_steps)
     return SPH_OK;
 }
 
+int sph_run_graph(sph_ctx *ctx, int64_t n_steps)
+{
+    if (!ctx || n_steps < 0) return SPH_ERR_INVALID_ARG;
+    if (ctx->stream == nullptr || ctx->stream == cudaStreamLegacy ||
+        ctx->stream == cudaStreamPerThread)
+        return SPH_ERR_INVALID_ARG;
+    int64_t k = 0;
+    for (; k + 2 <= n_steps; k += 2) {
+        const int c = ctx->cur;
+        if (!ctx->graph[c]) {
+            // capture two steps: the buffers swap every step, so the pair is periodic
+            cudaGraph_t g = nullptr;
+            long long before = ctx->launches;
+            if (check_cuda(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal)))
+                return SPH_ERR_CUDA;
+            int rc = sph_run(ctx, 2);
+            cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
+            if (rc || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                ctx->cur = c;
+                return rc ? rc : SPH_ERR_CUDA;
+            }
+            e = cudaGraphInstantiate(&ctx->graph[c], g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                ctx->graph[c] = nullptr;
+                ctx->cur = c;
+                return SPH_ERR_CUDA;
+            }
+            ctx->graph_launches[c] = ctx->launches - before;
+            ctx->launches = before;
+            ctx->cur = c;   // capture recorded the work; nothing ran yet
+        }
+        if (check_cuda(cudaGraphLaunch(ctx->graph[c], ctx->stream))) return SPH_ERR_CUDA;
+        ctx->launches += ctx->graph_launches[c];
+        // the two steps leave cur where it started
+    }
+    if (k < n_steps) return sph_run(ctx, 1);
+    ctx->nl_valid = ctx->pi_valid = false;
+    return SPH_OK;
+}
+
 int sph_get_state(sph_ctx *ctx, double *pos, double *vel, double *rho, double *vel_prev,
                   double *rho_prev)
 {
@@ -651,6 +693,12 @@ const char *sph_error_string(int code)
     }
 }
 
-void sph_destroy(sph_ctx *ctx) { free(ctx); }
+void sph_destroy(sph_ctx *ctx)
+{
+    if (!ctx) return;
+    for (int k = 0; k < 2; ++k)
+        if (ctx->graph[k]) cudaGraphExecDestroy(ctx->graph[k]);
+    free(ctx);
+}
 
 }  // extern "C"

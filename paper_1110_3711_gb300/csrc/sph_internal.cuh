@@ -113,6 +113,10 @@ struct sph_ctx {
     int device;
     int pi_grid_f, pi_grid_b;   // persistent grid sizes of the FP32 PI kernels
     bool branges_ready;         // boundary x-run table built for the current boundary list
+    // sph_run_graph: executable graphs of two consecutive steps, one per value
+    // of `cur` at the start, and the number of kernels each launches
+    cudaGraphExec_t graph[2];
+    long long graph_launches[2];
 };
 
 namespace sph {

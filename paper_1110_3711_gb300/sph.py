@@ -91,6 +91,7 @@ def lib():
                 "sph_interact": ([vp], i32),
                 "sph_update": ([vp, vp], i32),
                 "sph_run": ([vp, i64], i32),
+                "sph_run_graph": ([vp, i64], i32),
                 "sph_get_state": ([vp, vp, vp, vp, vp, vp], i32),
                 "sph_set_state": ([vp, vp, vp, vp, vp, vp], i32),
                 "sph_get_time": ([vp, vp, vp, vp], i32),
@@ -121,7 +122,7 @@ def lib():
 def exported_symbols():
     """Names the binding expects the library to export (all of include/sph.h)."""
     return ["sph_workspace_bytes", "sph_create", "sph_neighbour_list", "sph_interact",
-            "sph_update", "sph_run", "sph_get_state", "sph_set_state", "sph_get_time",
+            "sph_update", "sph_run", "sph_run_graph", "sph_get_state", "sph_set_state", "sph_get_time",
             "sph_status", "sph_get_neighbour_list", "sph_get_grid", "sph_get_forces",
             "sph_count_work", "sph_launch_count", "sph_checkpoint_bytes", "sph_save_state",
             "sph_load_state", "sph_neighbour_list_static", "sph_sensor_pressure",
@@ -200,6 +201,10 @@ def sph_update(ctx, want_dt=False):
 
 def sph_run(ctx, n_steps):
     _check(lib().sph_run(ctx, int(n_steps)), "sph_run")
+
+
+def sph_run_graph(ctx, n_steps):
+    _check(lib().sph_run_graph(ctx, int(n_steps)), "sph_run_graph")
 
 
 def sph_get_state(ctx, n, pos=None, vel=None, rho=None, vel_prev=None, rho_prev=None):
@@ -360,6 +365,9 @@ class Simulation:
 
     def run(self, n_steps):
         sph_run(self.ctx, n_steps)
+
+    def run_graph(self, n_steps):
+        sph_run_graph(self.ctx, n_steps)
 
     def get_state(self, with_prev=False):
         n = self.n

@@ -298,3 +298,28 @@ def test_tensile_rejected_where_unsupported(torch_mod):
     with pytest.raises(sph.SphError):
         sph.sph_adjoint_step(sim.ctx, lam, torch.zeros_like(lam),
                              torch.zeros(1, dtype=torch.float64, device="cuda"))
+
+
+@pytest.mark.parametrize("precision,steps", [("fp32", 10), ("fp32", 7), ("fp64", 6)])
+def test_graph_replay_equals_plain_steps(torch_mod, precision, steps):
+    """sph_run_graph (captured two-step CUDA graph) gives the bits of sph_run."""
+    torch = torch_mod
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        a = make_sim(c, precision, stream=s)
+        b = make_sim(c, precision, stream=s)
+        a.run(3)
+        b.run(3)
+        a.run(steps)
+        b.run_graph(steps)
+        b.run_graph(steps)   # second call replays the cached graphs
+        a.run(steps)
+    s.synchronize()
+    for x, y in zip(a.get_state(with_prev=True), b.get_state(with_prev=True)):
+        assert np.array_equal(x, y)
+    assert a.time()[2] == b.time()[2] == 3 + 2 * steps
+    legacy = make_sim(c, precision)      # torch's default stream is the legacy one
+    with pytest.raises(sph.SphError):
+        legacy.run_graph(2)
