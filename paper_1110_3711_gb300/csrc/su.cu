@@ -33,13 +33,15 @@ template <typename Real> struct V4T;
 template <> struct V4T<float> { typedef float4 T; };
 template <> struct V4T<double> { typedef double4_32a T; };
 
+// Fluid particles in blocks [0, fblocks), boundary particles after them.
 template <typename Real>
 __global__ void __launch_bounds__(256)
-k_su_fluid(int nf, DevParams P, const int32_t *__restrict__ fstart, double *__restrict__ x,
-           double *__restrict__ y, double *__restrict__ z, Real *__restrict__ vx,
-           Real *__restrict__ vy, Real *__restrict__ vz, Real *__restrict__ vmx,
-           Real *__restrict__ vmy, Real *__restrict__ vmz, Real *__restrict__ rho,
-           Real *__restrict__ rhom, const typename V4T<Real>::T *__restrict__ acc, Scalars *sc)
+k_su(int nf, int nb, int fblocks, DevParams P, const int32_t *__restrict__ fstart,
+     const int32_t *__restrict__ bstart, double *__restrict__ x, double *__restrict__ y,
+     double *__restrict__ z, Real *__restrict__ vx, Real *__restrict__ vy, Real *__restrict__ vz,
+     Real *__restrict__ vmx, Real *__restrict__ vmy, Real *__restrict__ vmz,
+     Real *__restrict__ rho, Real *__restrict__ rhom, const typename V4T<Real>::T *__restrict__ acc,
+     Real *__restrict__ brho, Real *__restrict__ brhom, const Real *__restrict__ bar, Scalars *sc)
 {
     __shared__ double sdt;
     __shared__ int seuler;
@@ -48,61 +50,55 @@ k_su_fluid(int nf, DevParams P, const int32_t *__restrict__ fstart, double *__re
         seuler = ((sc->step + 1) % P.euler_every) == 0;
     }
     __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nf || i >= fstart[P.ncells]) return;
     const double dt = sdt;
     const Real dtr = (Real)dt;
-    const double hdt2 = 0.5 * dt * dt;
-    typename V4T<Real>::T f = acc[i];
-    Real v0 = vx[i], v1 = vy[i], v2 = vz[i];
-    x[i] = x[i] + dt * (double)v0 + hdt2 * (double)f.x;
-    y[i] = y[i] + dt * (double)v1 + hdt2 * (double)f.y;
-    z[i] = z[i] + dt * (double)v2 + hdt2 * (double)f.z;
-    Real r = rho[i];
-    Real nv0, nv1, nv2, nr;
-    if (seuler) {
-        nv0 = v0 + dtr * f.x;
-        nv1 = v1 + dtr * f.y;
-        nv2 = v2 + dtr * f.z;
-        nr = r + dtr * f.w;
+    const Real dt2 = (Real)(2.0 * dt);
+    bool nan = false;
+    if ((int)blockIdx.x < fblocks) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i < nf && i < fstart[P.ncells]) {
+            typename V4T<Real>::T f = acc[i];
+            Real v0 = vx[i], v1 = vy[i], v2 = vz[i];
+            // x^{n+1} = x^n + (dt v^n + dt^2/2 F^n): the increment in the precision
+            // of the form, the accumulation always in float64
+            const Real hdt2 = (Real)(0.5 * dt * dt);
+            x[i] = x[i] + (double)(dtr * v0 + hdt2 * f.x);
+            y[i] = y[i] + (double)(dtr * v1 + hdt2 * f.y);
+            z[i] = z[i] + (double)(dtr * v2 + hdt2 * f.z);
+            Real r = rho[i];
+            Real nv0, nv1, nv2, nr;
+            if (seuler) {
+                nv0 = v0 + dtr * f.x;
+                nv1 = v1 + dtr * f.y;
+                nv2 = v2 + dtr * f.z;
+                nr = r + dtr * f.w;
+            } else {
+                nv0 = vmx[i] + dt2 * f.x;
+                nv1 = vmy[i] + dt2 * f.y;
+                nv2 = vmz[i] + dt2 * f.z;
+                nr = rhom[i] + dt2 * f.w;
+            }
+            vmx[i] = v0; vmy[i] = v1; vmz[i] = v2;
+            vx[i] = nv0; vy[i] = nv1; vz[i] = nv2;
+            rhom[i] = r;
+            rho[i] = nr;
+            nan = !(nr == nr) || !(nv0 == nv0) || !(nv1 == nv1) || !(nv2 == nv2);
+        }
     } else {
-        const Real dt2 = (Real)(2.0 * dt);
-        nv0 = vmx[i] + dt2 * f.x;
-        nv1 = vmy[i] + dt2 * f.y;
-        nv2 = vmz[i] + dt2 * f.z;
-        nr = rhom[i] + dt2 * f.w;
+        const int i = (blockIdx.x - fblocks) * blockDim.x + threadIdx.x;
+        if (i < nb && i < bstart[P.ncells]) {
+            Real r = brho[i];
+            Real nr = seuler ? r + dtr * bar[i] : brhom[i] + dt2 * bar[i];
+            if (P.clamp && nr < (Real)P.rho0) nr = (Real)P.rho0;
+            brhom[i] = r;
+            brho[i] = nr;
+            nan = !(nr == nr);
+        }
     }
-    vmx[i] = v0; vmy[i] = v1; vmz[i] = v2;
-    vx[i] = nv0; vy[i] = nv1; vz[i] = nv2;
-    rhom[i] = r;
-    rho[i] = nr;
-    if (!(nr == nr) || !(nv0 == nv0) || !(nv1 == nv1) || !(nv2 == nv2))
-        atomicOr(&sc->flags, SPH_FLAG_NAN);
+    if (nan) atomicOr(&sc->flags, SPH_FLAG_NAN);
 }
 
-template <typename Real>
-__global__ void __launch_bounds__(256)
-k_su_boundary(int nb, DevParams P, const int32_t *__restrict__ bstart, Real *__restrict__ rho,
-              Real *__restrict__ rhom, const Real *__restrict__ bar, Scalars *sc)
-{
-    __shared__ double sdt;
-    __shared__ int seuler;
-    if (threadIdx.x == 0) {
-        sdt = step_dt(P, sc);
-        seuler = ((sc->step + 1) % P.euler_every) == 0;
-    }
-    __syncthreads();
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= nb || i >= bstart[P.ncells]) return;
-    const Real dtr = (Real)sdt;
-    Real r = rho[i];
-    Real nr = seuler ? r + dtr * bar[i] : rhom[i] + (Real)(2.0 * sdt) * bar[i];
-    if (P.clamp && nr < (Real)P.rho0) nr = (Real)P.rho0;
-    rhom[i] = r;
-    rho[i] = nr;
-    if (!(nr == nr)) atomicOr(&sc->flags, SPH_FLAG_NAN);
-}
-
+// One thread, after the update: advance time and step, clear the maxima.
 __global__ void k_finalize(DevParams P, Scalars *sc)
 {
     double dt = step_dt(P, sc);
@@ -123,14 +119,13 @@ static int su_t(sph_ctx *ctx)
     int nf = (int)ctx->nf, nb = (int)ctx->nb;
     int c = ctx->cur;
     const int T = 256;
-    if (nf > 0)
-        SPH_LAUNCH(ctx, k_su_fluid<Real>, (nf + T - 1) / T, T, 0, st, nf, ctx->dp, w.fstart,
-                   w.x[c], w.y[c], w.z[c], (Real *)w.vx[c], (Real *)w.vy[c], (Real *)w.vz[c],
-                   (Real *)w.vmx[c], (Real *)w.vmy[c], (Real *)w.vmz[c], (Real *)w.rho[c],
-                   (Real *)w.rhom[c], (const typename V4T<Real>::T *)w.acc, w.sc);
-    if (nb > 0)
-        SPH_LAUNCH(ctx, k_su_boundary<Real>, (nb + T - 1) / T, T, 0, st, nb, ctx->dp, w.bstart,
-                   (Real *)w.brho, (Real *)w.brhom, (const Real *)w.bar, w.sc);
+    const int fblocks = (nf + T - 1) / T, bblocks = (nb + T - 1) / T;
+    SPH_LAUNCH(ctx, k_su<Real>, fblocks + bblocks > 0 ? fblocks + bblocks : 1, T, 0, st, nf, nb,
+               fblocks, ctx->dp, w.fstart, w.bstart, w.x[c], w.y[c], w.z[c], (Real *)w.vx[c],
+               (Real *)w.vy[c], (Real *)w.vz[c], (Real *)w.vmx[c], (Real *)w.vmy[c],
+               (Real *)w.vmz[c], (Real *)w.rho[c], (Real *)w.rhom[c],
+               (const typename V4T<Real>::T *)w.acc, (Real *)w.brho, (Real *)w.brhom,
+               (const Real *)w.bar, w.sc);
     SPH_LAUNCH(ctx, k_finalize, 1, 1, 0, st, ctx->dp, w.sc);
     return check_cuda(cudaGetLastError());
 }
