@@ -203,39 +203,38 @@ k_scan_reduce(const uint32_t *__restrict__ in, int64_t n, uint32_t *__restrict__
     }
 }
 
-// single block: exclusive scan of the partials in place
-__global__ void __launch_bounds__(kScanBlock) k_scan_partials(uint32_t *part, int64_t np)
-{
-    __shared__ uint32_t smem[33];
-    uint32_t carry = 0;
-    for (int64_t b = 0; b < np; b += kScanBlock) {
-        int64_t i = b + threadIdx.x;
-        uint32_t v = i < np ? part[i] : 0u;
-        uint32_t ex = block_exclusive(v, smem);
-        __syncthreads();
-        uint32_t tot = smem[32];
-        if (i < np) part[i] = carry + ex;
-        carry += tot;
-        __syncthreads();
-    }
-}
-
+// Down-sweep: every block adds the sum of the partials of the blocks before it
+// (a block reduction over at most a few thousand values) to its own exclusive
+// scan, so no separate pass over the partials is needed.
 __global__ void __launch_bounds__(kScanBlock)
 k_scan_down(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *__restrict__ part)
 {
     __shared__ uint32_t smem[33];
-    int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    __shared__ uint32_t base_s;
+    uint32_t b = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += kScanBlock) b += part[k];
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanBlock / 32; ++w) t += smem[w];
+        base_s = t;
+    }
+    __syncthreads();
+    const uint32_t base = base_s;
+    int64_t start = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     uint32_t v[kScanItems];
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        v[k] = base + k < n ? in[base + k] : 0u;
+        v[k] = start + k < n ? in[start + k] : 0u;
         s += v[k];
     }
-    uint32_t ex = block_exclusive(s, smem) + part[blockIdx.x];
+    uint32_t ex = block_exclusive(s, smem) + base;
 #pragma unroll
     for (int k = 0; k < kScanItems; ++k) {
-        if (base + k < n) out[base + k] = ex;
+        if (start + k < n) out[start + k] = ex;
         ex += v[k];
     }
 }
@@ -248,7 +247,6 @@ int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t 
     if (n <= 0) return SPH_OK;
     int64_t blocks = (n + kScanTile - 1) / kScanTile;
     SPH_LAUNCH(ctx, k_scan_reduce, (unsigned)blocks, kScanBlock, 0, st, in, n, partials);
-    SPH_LAUNCH(ctx, k_scan_partials, 1, kScanBlock, 0, st, partials, blocks);
     SPH_LAUNCH(ctx, k_scan_down, (unsigned)blocks, kScanBlock, 0, st, in, out, n, partials);
     return check_cuda(cudaGetLastError());
 }
@@ -265,11 +263,9 @@ int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t 
     // ping-pong so that the last pass lands in (kout, vout)
     const uint32_t *ks = kin, *vs = vin;
     for (int p = 0; p < passes; ++p) {
-        bool last = p == passes - 1;
         bool to_out = ((passes - 1 - p) % 2) == 0;
         uint32_t *kd = to_out ? kout : ktmp;
         uint32_t *vd = to_out ? vout : vtmp;
-        (void)last;
         int shift = 8 * p;
         SPH_LAUNCH(ctx, k_radix_hist, tiles, RS_THREADS, 0, st, ks, n, shift, tiles, w.radix_hist);
         int rc = exclusive_scan_u32(ctx, w.radix_hist, w.radix_hist, (int64_t)256 * tiles,
