@@ -83,7 +83,8 @@ typedef struct sph_params {
     double h;             /* smoothing length (m); support radius 2h */
     double cell_size;     /* cell edge (m), normally 2h */
     double rho0;          /* reference density (kg/m^3) */
-    double gamma;         /* Tait exponent */
+    double gamma;         /* Tait exponent (SPH_FP32_SPLIT: 7 only, as in Table 1;
+                             other values give SPH_ERR_INVALID_ARG) */
     double c0;            /* speed of sound at rho0 (m/s) */
     double alpha;         /* artificial viscosity coefficient */
     double eta2_coef;     /* eta^2 = eta2_coef * h^2 */

@@ -37,6 +37,9 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
         (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) ||
         p->pi_kernel < SPH_PI_WARP || p->pi_kernel > SPH_PI_THREAD_FASTCELLS)
         return SPH_ERR_INVALID_ARG;
+    // the float32 PI kernels take the sound speed as c0 (rho / rho0)^3, the
+    // Tait form of gamma = 7 (Table 1)
+    if (p->precision == SPH_FP32_SPLIT && p->gamma != 7.0) return SPH_ERR_INVALID_ARG;
     const bool tensile = p->tensile_eps != 0.0 || p->tensile_pos != 0.0;
     if (tensile && (p->tensile_n < 1 || p->tensile_n > 16 || !(p->dp > 0) ||
                     (p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_WARP)))
@@ -102,6 +105,14 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
     d.kA = (float)d.kA64;
     d.kB = (float)d.kB64;
     d.aDf = (float)aD;
+    d.s_hf = (float)(p.cell_size / p.h);
+    d.eta2_h2f = (float)p.eta2_coef;
+    d.gw1 = (float)(2.25 * d.kA64 * p.h / d.kB64);
+    d.gw0 = (float)(-3.0 * d.kA64 * p.h / d.kB64);
+    d.nmkBf = (float)(-p.mass * d.kB64);
+    d.mkBf = (float)(p.mass * d.kB64);
+    d.kcf = (float)(-p.alpha * p.c0 / (p.rho0 * p.rho0 * p.rho0));
+    d.nalphaf = (float)(-p.alpha);
     d.tensile = (p.tensile_eps != 0.0 || p.tensile_pos != 0.0) ? 1 : 0;
     d.tensile_n = (int)p.tensile_n;
     d.tens_eps = p.tensile_eps;

@@ -10,12 +10,12 @@
 //      fluid targets): cells x-1..x+1 of every (y, z) row are one index range
 //      (Section 4.4, Fig. 10);
 //   2. stages the candidates of those runs in shared memory, already shifted
-//      into the frame of the target cell (candidate offset + cell delta * s),
-//      with |x_b|^2 beside them;
+//      into the frame of the target cell and measured in units of h
+//      ((candidate offset + cell delta * s) / h), with |x_b|^2 beside them;
 //   3. tests all candidates against all 32 targets in lockstep: the warp reads
 //      one candidate (a shared-memory broadcast) and each lane evaluates
-//      |x_b|^2 - 2 x_a.x_b - (4h^2 - |x_a|^2) (three FMAs and a subtraction; it
-//      is negative exactly when |x_a - x_b|^2 < 4h^2 up to float32 rounding)
+//      |x_b|^2 - 2 x_a.x_b - (4 - |x_a|^2) (three FMAs and a subtraction; it
+//      is negative exactly when |x_a - x_b| < 2h up to float32 rounding)
 //      and shifts its sign bit into a hit mask;
 //   4. walks its own hit bits (about 112 real neighbours per lane, so lanes
 //      stay balanced) and evaluates the pair terms of the oracle (cubic-spline
@@ -64,8 +64,36 @@ struct Acc {
     float ax, ay, az, ar, vis;
 };
 
+// Approximate reciprocal and reciprocal square root (PTX rcp.approx and
+// rsqrt.approx, relative error about 2^-23).  Their arguments here are normal
+// numbers (densities, r'^2 + eta^2/h^2 >= eta^2/h^2, r'^2 clamped at 1e-30),
+// so flushing subnormals changes nothing.
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // Terms of one ordered pair a <- b (see the oracle): momentum sum, continuity
-// sum and the viscous dt term.
+// sum and the viscous dt term, in units of h.  With r' = r / h and
+// q = |r'|, the cubic-spline gradient is grad_a W = F r with
+// F = (kB / h) F'', F'' = (kA h / kB)(2.25 q - 3) for q < 1 and (2 - q)^2 / q
+// for 1 <= q < 2, so that
+//   momentum:   -(P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab) F r   = -kB (...) F'' r'
+//   continuity:  v_ab . F r                                =  kB (v_ab . r') F''
+//   viscosity:  mu_ab = h v_ab.r / (r^2 + eta^2)          = v_ab.r' / (q^2 + eta^2/h^2)
+//   Pi_ab = -alpha (c_a + c_b) mu_ab / (rho_a + rho_b)     (mu_ab < 0, else 0).
+// The sums hold (...) F'' r' and (v_ab . r') F''; the constant factors -m kB
+// and m kB are applied once per target.  cpa = -alpha c_a; -alpha c_b is
+// kcf rho_b^3 (Tait sound speed with gamma = 7, c = c0 (rho / rho0)^3).
 // Tensile correction of Monaghan (2000): R_ab (W(r)/W(dp))^n (see the FP64 form).
 __device__ __forceinline__ float tensile32(const DevParams &P, float q, float pra, float prb)
 {
@@ -80,25 +108,28 @@ __device__ __forceinline__ float tensile32(const DevParams &P, float q, float pr
 
 template <bool MOMENTUM, bool TENSILE>
 __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, float za,
-                                     const float4 &pa, const float4 &va, float ca,
+                                     const float4 &pa, const float4 &va, float cpa,
                                      const float4 &b, const float4 &vb, float prb, Acc &o)
 {
-    float rx = xa - b.x, ry = ya - b.y, rz = za - b.z;
-    float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-    float r = r2 * rinv;
-    float q = r * P.invhf;
-    float t = 2.0f - q;
-    float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
-    float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
-    float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
-    float mu = __fdividef(P.hf * vdr, r2 + P.eta2f);
+    const float rx = xa - b.x, ry = ya - b.y, rz = za - b.z;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+    const float q = r2 * rinv;
+    const float t = 2.0f - q;
+    const float F = q < 1.0f ? fmaf(P.gw1, q, P.gw0) : t * t * rinv;
+    const float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
+    const float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
+    const float mu = vdr * rcp_approx(r2 + P.eta2_h2f);
     if (MOMENTUM) {
-        float rb = vb.w * P.inv_rho0f;
-        float cb = P.c0f * rb * rb * rb;
-        float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
-        if (TENSILE) Pi += tensile32(P, q, pa.w, prb);
-        float coef = -(pa.w + prb + Pi) * F;
+        const float cc = fmaf(P.kcf, vb.w * vb.w * vb.w, cpa);
+        float coef;
+        if (TENSILE) {
+            const float Pi = cc * fminf(mu, 0.0f) * rcp_approx(va.w + vb.w) +
+                             tensile32(P, q, pa.w, prb);
+            coef = (pa.w + prb + Pi) * F;
+        } else {
+            coef = fmaf(cc * fminf(mu, 0.0f), rcp_approx(va.w + vb.w), pa.w + prb) * F;
+        }
         o.ax = fmaf(coef, rx, o.ax);
         o.ay = fmaf(coef, ry, o.ay);
         o.az = fmaf(coef, rz, o.az);
@@ -147,11 +178,11 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
         const int cx = (int)(c - cyz * (uint32_t)P.nx);
         const int cy = (int)(cyz % (uint32_t)P.ny);
         const int cz = (int)(cyz / (uint32_t)P.ny);
-        const float xa = pa.x, ya = pa.y, za = pa.z;
+        const float xa = pa.x * P.invhf, ya = pa.y * P.invhf, za = pa.z * P.invhf;
         const float m2x = -2.0f * xa, m2y = -2.0f * ya, m2z = -2.0f * za;
-        const float thr = active ? P.four_h2f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
+        const float thr = active ? 4.0f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
         const float ra = va.w * P.inv_rho0f;
-        const float ca = P.c0f * ra * ra * ra;
+        const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
 
         // ---- run table: lane r describes run r
         int K;
@@ -208,9 +239,9 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                     const int prev = r ? S.run[r - 1].x : 0;
                     const int j = ri.y + (s - prev);
                     const int cd = S.code[r];
-                    const float sx = j < ri.z ? -P.sf : (j < ri.w ? 0.0f : P.sf);
-                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.sf;
-                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.sf;
+                    const float sx = j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf);
+                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
+                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
                     float4 p;
                     if (MOMENTUM && (cd & 1)) {
                         p = bposp[j];
@@ -219,9 +250,9 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                         p = fposp[j];
                         v = fvelr[j];
                     }
-                    a.x = p.x + sx;
-                    a.y = p.y + sy;
-                    a.z = p.z + sz;
+                    a.x = fmaf(p.x, P.invhf, sx);
+                    a.y = fmaf(p.y, P.invhf, sy);
+                    a.z = fmaf(p.z, P.invhf, sz);
                     a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
                     pr = p.w;
                 } else {
@@ -263,23 +294,23 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                 if (m == 0u) break;
                 const int ls = q * 32 + __ffs(m) - 1;
                 m &= m - 1u;
-                pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, ca, S.A[ls], S.V[ls], S.Pr[ls], o);
+                pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, cpa, S.A[ls], S.V[ls], S.Pr[ls], o);
             }
             __syncwarp();
         }
 
         if (active) {
             if (MOMENTUM) {
-                const float ax = fmaf(P.massf, o.ax, P.gf[0]);
-                const float ay = fmaf(P.massf, o.ay, P.gf[1]);
-                const float az = fmaf(P.massf, o.az, P.gf[2]);
-                const float ar = P.massf * o.ar;
+                const float ax = fmaf(P.nmkBf, o.ax, P.gf[0]);
+                const float ay = fmaf(P.nmkBf, o.ay, P.gf[1]);
+                const float az = fmaf(P.nmkBf, o.az, P.gf[2]);
+                const float ar = P.mkBf * o.ar;
                 acc[i] = make_float4(ax, ay, az, ar);
                 const double f2 = (double)ax * ax + (double)ay * ay + (double)az * az;
                 f2max = fmax(f2max, f2);
                 bad |= !(f2 < INFINITY) || !(ar == ar);
             } else {
-                const float ar = P.massf * o.ar;
+                const float ar = P.mkBf * o.ar;
                 bar[i] = ar;
                 bad |= !(ar == ar);
             }

@@ -56,6 +56,10 @@ struct DevParams {
     float hf, invhf, four_h2f, eta2f, massf, alphaf, c0f, inv_rho0f, Bf, sf;
     float kA, kB;   // grad-W factor constants (see pi.cu)
     float aDf, tens_epsf, tens_posf, inv_wdpf;  // 1/(pi h^3) and the tensile constants
+    // the warp FP32 PI kernel works in units of h (see pi32.cu): s/h, eta^2/h^2,
+    // the grad-W branch q < 1 as F'' = gw1 q + gw0, the per-target factors
+    // -m kB (momentum) and m kB (continuity), and -alpha c0 / rho0^3
+    float s_hf, eta2_h2f, gw1, gw0, nmkBf, mkBf, kcf, nalphaf;
     float gf[3];
 };
 

@@ -47,6 +47,13 @@ def test_error_strings_and_workspace_on_cpu(libsph):
     bad.cell_size = c.params.h  # below the support 2h
     with pytest.raises(sph.SphError):
         sph.sph_workspace_bytes(bad, c.n_f, c.n_b)
+    g5 = sph.make_params(c.params, "fp32")
+    g5.gamma = 5.0  # the float32 sound speed is the gamma = 7 form
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(g5, c.n_f, c.n_b)
+    g5 = sph.make_params(c.params, "fp64")
+    g5.gamma = 5.0
+    assert sph.sph_workspace_bytes(g5, c.n_f, c.n_b) > 0
 
 
 def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
