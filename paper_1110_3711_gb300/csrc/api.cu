@@ -80,7 +80,11 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
     double aD = 1.0 / (M_PI * p.h * p.h * p.h);
     d.kA64 = aD / (p.h * p.h);
     d.kB64 = -0.75 * aD / p.h;
+    d.cell_af = (float)(1.0 / p.cell_size);
+    d.cell_eabsf = (float)fmax(0x1p-60, 0x1p-124 / p.cell_size);  // inf: always the float64 path
     for (int k = 0; k < 3; ++k) {
+        d.cell_bf[k] = (float)(p.dom_min[k] / p.cell_size);
+        d.cell_babsf[k] = fabsf(d.cell_bf[k]);
         d.g[k] = p.g[k];
         d.dom_min[k] = p.dom_min[k];
         d.gf[k] = (float)p.g[k];

@@ -24,11 +24,44 @@ namespace sph {
 
 // ------------------------------------------------------------------ cells --
 
-// floor((x - mn) / s) with IEEE division, computed through the reciprocal and
-// corrected by a true division when the quotient is within 1e-9 of an integer
-// (the only case where the two can round to different sides).
-__device__ __forceinline__ int axis_cell(double x, double mn, double s, double inv_s, int n)
+// float32 value of x with its 24 leading significand bits (the rest cut off,
+// so |xf - x| < 2^-23 |x|), built from the bit pattern with integer operations
+// only; 0 below the normal float range, NaN above it and for inf or NaN.
+__device__ __forceinline__ float trunc_to_float(double x)
 {
+    const uint32_t hi = (uint32_t)__double2hiint(x), lo = (uint32_t)__double2loint(x);
+    const uint32_t e = (hi >> 20) & 0x7ffu;
+    if (e < 897u) return 0.0f;
+    if (e > 1150u) return __int_as_float(0x7fffffff);
+    return __uint_as_float((hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xfffffu) << 3) |
+                           (lo >> 29));
+}
+
+// floor((x - mn) / s) as the float64 definition gives it: d = x - mn rounded,
+// then d / s with IEEE division, then floor; -1 outside [0, n).
+//
+// Fast path, float32 and integer operations only: e = xf (1/s) - mn/s with the
+// float32 constants a = RN(1/s), b = RN(mn/s).  Each of xf, a, b and the fused
+// multiply-add is within 2^-23 (relative) of its exact value, so
+// |e - (x - mn)/s| < 2^-20 (|e| + |mn/s|).  The margin E below is twice that,
+// plus eabs >= 2^-124 / s, the largest error of an input below the float range
+// flushed to 0; when e - E and e + E floor
+// to the same integer, no integer lies within the error of e, so floor(e) is
+// floor((x - mn)/s), and also floor of the rounded float64 quotient, whose
+// relative error (about 2^-52) is far inside the margin.  Otherwise (a
+// quotient within about 2^-19 relative of an integer, |e| >= 2^22, NaN) the
+// float64 path decides: reciprocal, and a true division when the quotient is
+// within 1e-9 of an integer (the only case where the two can round to
+// different sides).
+__device__ __forceinline__ int axis_cell(double x, double mn, double s, double inv_s, int n,
+                                         float a, float b, float babs, float eabs)
+{
+    const float e = fmaf(trunc_to_float(x), a, -b);
+    if (fabsf(e) < 4194304.0f) {  // 2^22; false for NaN
+        const float E = fmaf(0x1p-19f, fabsf(e) + babs, eabs);
+        const int lo = __float2int_rd(e - E), hi = __float2int_rd(e + E);
+        if (lo == hi) return (lo >= 0 && lo < n) ? lo : -1;
+    }
     double d = x - mn;
     double t = d * inv_s;
     double f = floor(t);
@@ -39,9 +72,12 @@ __device__ __forceinline__ int axis_cell(double x, double mn, double s, double i
 
 __device__ __forceinline__ uint32_t cell_of(const DevParams &P, double x, double y, double z)
 {
-    int cx = axis_cell(x, P.dom_min[0], P.s, P.inv_s, P.nx);
-    int cy = axis_cell(y, P.dom_min[1], P.s, P.inv_s, P.ny);
-    int cz = axis_cell(z, P.dom_min[2], P.s, P.inv_s, P.nz);
+    int cx = axis_cell(x, P.dom_min[0], P.s, P.inv_s, P.nx, P.cell_af, P.cell_bf[0], P.cell_babsf[0],
+                       P.cell_eabsf);
+    int cy = axis_cell(y, P.dom_min[1], P.s, P.inv_s, P.ny, P.cell_af, P.cell_bf[1], P.cell_babsf[1],
+                       P.cell_eabsf);
+    int cz = axis_cell(z, P.dom_min[2], P.s, P.inv_s, P.nz, P.cell_af, P.cell_bf[2], P.cell_babsf[2],
+                       P.cell_eabsf);
     if (cx < 0 || cy < 0 || cz < 0) return P.ncells;
     return (uint32_t)cx + (uint32_t)P.nx * ((uint32_t)cy + (uint32_t)P.ny * (uint32_t)cz);
 }

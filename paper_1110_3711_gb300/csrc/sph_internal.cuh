@@ -60,6 +60,9 @@ struct DevParams {
     // the grad-W branch q < 1 as F'' = gw1 q + gw0, the per-target factors
     // -m kB (momentum) and m kB (continuity), and -alpha c0 / rho0^3
     float s_hf, eta2_h2f, gw1, gw0, nmkBf, mkBf, kcf, nalphaf;
+    // cell of a position from a float32 estimate (see nl.cu): 1/s, min/s and
+    // |min/s| per axis, and the error bound of positions flushed to 0
+    float cell_af, cell_bf[3], cell_babsf[3], cell_eabsf;
     float gf[3];
 };
 

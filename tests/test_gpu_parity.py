@@ -78,6 +78,35 @@ def test_nl_after_motion_and_out_of_grid(torch_mod, O):
     assert sim.status(clear=True) & FLAG_OUT_OF_GRID
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_nl_cell_faces_bit_exact(torch_mod, O, precision):
+    """Positions on cell faces, one or two ulps either side of them, within
+    1e-9 (relative) of them and inside the cells, including the faces of the
+    grid itself: every cell is floor((x - min) / s) of the float64 division."""
+    c = random_cloud(20000 + 17, box=0.3, dp=0.01, n_b=17, seed=11)
+    p = c.params
+    dims = np.asarray(O.grid(p))
+    rng = np.random.default_rng(12)
+    n = c.n_f
+    k = rng.integers(-1, dims + 2, size=(n, 3))
+    base = np.asarray(p.dom_min) + k * p.cell_size
+    mode = rng.integers(0, 7, size=(n, 3))
+    x = base.copy()
+    x = np.where(mode == 1, np.nextafter(base, np.inf), x)
+    x = np.where(mode == 2, np.nextafter(base, -np.inf), x)
+    x = np.where(mode == 3, np.nextafter(np.nextafter(base, np.inf), np.inf), x)
+    x = np.where(mode == 4, np.nextafter(np.nextafter(base, -np.inf), -np.inf), x)
+    x = np.where(mode == 5, base * (1.0 + rng.normal(0.0, 1e-9, size=base.shape)), x)
+    x = np.where(mode == 6, base + rng.uniform(0.0, p.cell_size, size=base.shape), x)
+    pos = c.pos.copy()
+    pos[:n] = x
+    c2 = type(c)(**{**c.__dict__, "pos": pos})
+    sim = make_sim(c2, precision)
+    sim.neighbour_list()
+    _check_nl(O, sim, c2, pos)
+    sim.status(clear=True)
+
+
 def test_work_counts_exact(torch_mod, O):
     c = dam_break(0.02)
     sim = make_sim(c, "fp32")
