@@ -16,6 +16,7 @@ max over ranks and the value counts the steps of all ranks.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import math
@@ -159,6 +160,13 @@ def barrier(world):
 
 
 # ------------------------------------------------------------- GPU timing --
+
+def fine_cells(case):
+    """The same case on cells of edge h (half the support), the paper's finer
+    cells (optimisation G-F)."""
+    p = dataclasses.replace(case.params, cell_size=case.params.h)
+    return type(case)(**{**case.__dict__, "params": p})
+
 
 def pi_flops(counts):
     """Algorithmic FLOPs of one PI call for the exact candidate and pair counts."""
@@ -460,16 +468,27 @@ def main():
     extra = {}
     if args.ablation_steps > 0:
         # the paper's GPU design on the same workload (Section 4, Fig. 11): one
-        # thread per particle, ranges from CellBeginEnd or precomputed per cell
-        # thread per particle, ranges from CellBeginEnd or precomputed per cell;
-        # all three designs over the same steps from the initial state
+        # thread per particle, ranges from CellBeginEnd or precomputed per cell,
+        # and the same on cells of edge h (optimisation G-F, 125-cell search);
+        # all designs over the same steps from the initial state
         abl = {"steps": args.ablation_steps}
-        for kname in ("warp", "thread", "thread_fastcells"):
-            s_a, r_a = run_form(torch, case, "fp32", args.ablation_steps, 3, flush, world,
+        fine = fine_cells(case)
+        for name, kname, cs in (("warp", "warp", case), ("thread", "thread", case),
+                                ("thread_fastcells", "thread_fastcells", case),
+                                ("thread_hcells", "thread", fine)):
+            s_a, r_a = run_form(torch, cs, "fp32", args.ablation_steps, 3, flush, world,
                                 pi_kernel=kname)
             del s_a
-            abl[kname] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
-                          "stage_ms": r_a["stage_ms"]}
+            abl[name] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
+                         "stage_ms": r_a["stage_ms"],
+                         "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
+        if args.fp64_steps > 0:
+            s_a, r_a = run_form(torch, fine, "fp64", args.fp64_steps, 3, flush, world)
+            del s_a
+            abl["fp64"] = {"steps_per_s": r64["steps_per_s"], "pi_ms": r64["pi_ms"],
+                           "candidates_per_step": r64["counts"][0] + r64["counts"][2]}
+            abl["fp64_hcells"] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
+                                  "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
         extra["pi_kernel_ablation"] = abl
     if not args.no_5m and args.workload != "dam5m":
         case5 = dam_break(WORKLOADS["dam5m"]["dp"])

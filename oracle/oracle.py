@@ -105,6 +105,15 @@ def params(p) -> OrParams:
     return o
 
 
+def _searchable(p):
+    """Parameters for a call that searches neighbours: the oracle visits the 27
+    cells around a particle, which hold its whole support only when the cell
+    edge is at least 2h."""
+    if not p.cell_size >= 2.0 * p.h * (1.0 - 1e-12):
+        raise ValueError("oracle neighbour search needs cell_size >= 2h")
+    return params(p)
+
+
 def grid(p):
     dims = np.zeros(3, np.int64)
     rc = lib().or_grid(C.byref(params(p)), _ptr(dims))
@@ -157,7 +166,7 @@ def pairs(p, n_f, n_b, pos, cap=None):
     pa = np.zeros(cap, np.int64)
     pb = np.zeros(cap, np.int64)
     cnt = np.zeros(1, np.int64)
-    rc = lib().or_pairs(C.byref(params(p)), n_f, n_b, _ptr(pos), _ptr(pa), _ptr(pb), cap, _ptr(cnt))
+    rc = lib().or_pairs(C.byref(_searchable(p)), n_f, n_b, _ptr(pos), _ptr(pa), _ptr(pb), cap, _ptr(cnt))
     if rc:
         raise MemoryError("or_pairs")
     k = int(cnt[0])
@@ -176,7 +185,7 @@ def interact(p, n_f, n_b, pos, vel, rho, nthreads=0):
     ar = np.zeros(max(n, 1), np.float64)
     vm = np.zeros(1, np.float64)
     counts = np.zeros(4, np.int64)
-    nout = lib().or_interact(C.byref(params(p)), n_f, n_b, _ptr(pos), _ptr(vel), _ptr(rho),
+    nout = lib().or_interact(C.byref(_searchable(p)), n_f, n_b, _ptr(pos), _ptr(vel), _ptr(rho),
                              _ptr(ace), _ptr(ar), _ptr(vm), _ptr(counts), int(nthreads))
     if nout < 0:
         raise MemoryError("or_interact")
@@ -195,7 +204,7 @@ def interact_sampled(p, n_f, n_b, pos, vel, rho, stride, nthreads=0):
     vm = np.zeros(1, np.float64)
     counts = np.zeros(4, np.int64)
     secs = np.zeros(2, np.float64)
-    nout = lib().or_interact_sampled(C.byref(params(p)), n_f, n_b, _ptr(pos), _ptr(vel), _ptr(rho),
+    nout = lib().or_interact_sampled(C.byref(_searchable(p)), n_f, n_b, _ptr(pos), _ptr(vel), _ptr(rho),
                                      _ptr(ace), _ptr(ar), _ptr(vm), _ptr(counts), int(nthreads),
                                      int(stride), _ptr(secs))
     if nout < 0:
@@ -245,7 +254,7 @@ class State:
         """One NL -> PI -> SU step; returns dt."""
         dt = np.zeros(1, np.float64)
         counts = np.zeros(4, np.int64)
-        nout = lib().or_step(C.byref(params(self.p)), self.n_f, self.n_b, self.step_index,
+        nout = lib().or_step(C.byref(_searchable(self.p)), self.n_f, self.n_b, self.step_index,
                              _ptr(self.pos), _ptr(self.vel), _ptr(self.velm1),
                              _ptr(self.rho), _ptr(self.rhom1), _ptr(dt), _ptr(counts),
                              int(nthreads))
@@ -272,6 +281,6 @@ def sensor_pressure(p, n_f, pos, rho, spos):
     rho = np.ascontiguousarray(rho, np.float64)
     spos = np.ascontiguousarray(spos, np.float64)
     out = np.zeros(spos.shape[0], np.float64)
-    lib().or_sensor_pressure(C.byref(params(p)), n_f, _ptr(pos), _ptr(rho), spos.shape[0],
+    lib().or_sensor_pressure(C.byref(_searchable(p)), n_f, _ptr(pos), _ptr(rho), spos.shape[0],
                              _ptr(spos), _ptr(out))
     return out

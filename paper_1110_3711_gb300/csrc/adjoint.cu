@@ -130,14 +130,16 @@ __device__ __forceinline__ void cell_coords(const DevParams &P, uint32_t c, int 
     *cz = (int)(t / (uint32_t)P.ny);
 }
 
-// Visit the candidates j of the 9 x-runs of a list around cell (cx, cy, cz).
+// Visit the candidates j of the x-runs of a list around cell (cx, cy, cz): 9
+// runs of 3 cells, or 25 runs of 5 cells when cells are finer than 2h.
 #define FOR_RUNS(P, cx, cy, cz, start, j, ...)                                    \
     {                                                                              \
-        int x0_ = max((cx) - 1, 0), x1_ = min((cx) + 1, (P).nx - 1);               \
-        for (int dz_ = -1; dz_ <= 1; ++dz_) {                                      \
+        const int R_ = (P).reach;                                                  \
+        int x0_ = max((cx) - R_, 0), x1_ = min((cx) + R_, (P).nx - 1);             \
+        for (int dz_ = -R_; dz_ <= R_; ++dz_) {                                    \
             int z_ = (cz) + dz_;                                                   \
             if (z_ < 0 || z_ >= (P).nz) continue;                                  \
-            for (int dy_ = -1; dy_ <= 1; ++dy_) {                                  \
+            for (int dy_ = -R_; dy_ <= R_; ++dy_) {                                \
                 int y_ = (cy) + dy_;                                               \
                 if (y_ < 0 || y_ >= (P).ny) continue;                              \
                 int row_ = (P).nx * (y_ + (P).ny * z_);                            \
@@ -417,11 +419,12 @@ __global__ void k_sensor(int S, DevParams P, const double *__restrict__ spos,
     double num = 0.0, den = 0.0;
     if (cx >= 0 && cy >= 0 && cz >= 0) {
         const double s2 = 4.0 * P.h * P.h;
-        int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
-        for (int dz = -1; dz <= 1; ++dz) {
+        const int R = P.reach;
+        int x0 = max(cx - R, 0), x1 = min(cx + R, P.nx - 1);
+        for (int dz = -R; dz <= R; ++dz) {
             int zz = cz + dz;
             if (zz < 0 || zz >= P.nz) continue;
-            for (int dy = -1; dy <= 1; ++dy) {
+            for (int dy = -R; dy <= R; ++dy) {
                 int yy = cy + dy;
                 if (yy < 0 || yy >= P.ny) continue;
                 int row = P.nx * (yy + P.ny * zz);

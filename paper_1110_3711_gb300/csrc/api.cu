@@ -28,10 +28,17 @@ struct Bump {
     }
 };
 
+// Cells searched on each side of a particle's own cell: the support 2h spans
+// one cell of edge >= 2h and two cells of edge in [h, 2h).
+int cell_reach(const sph_params &p)
+{
+    return p.cell_size >= 2.0 * p.h * (1.0 - 1e-12) ? 1 : 2;
+}
+
 int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells)
 {
     if (!p || nf < 0 || nb < 0) return SPH_ERR_INVALID_ARG;
-    if (!(p->h > 0) || !(p->cell_size >= 2.0 * p->h * (1.0 - 1e-12)) || !(p->rho0 > 0) ||
+    if (!(p->h > 0) || !(p->cell_size >= p->h * (1.0 - 1e-12)) || !(p->rho0 > 0) ||
         !(p->gamma > 0) || !(p->c0 > 0) || !(p->mass > 0) || !(p->cfl > 0) ||
         !(p->alpha >= 0) || !(p->eta2_coef > 0) || p->verlet_euler_every < 1 ||
         (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) ||
@@ -40,6 +47,10 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
     // the float32 PI kernels take the sound speed as c0 (rho / rho0)^3, the
     // Tait form of gamma = 7 (Table 1)
     if (p->precision == SPH_FP32_SPLIT && p->gamma != 7.0) return SPH_ERR_INVALID_ARG;
+    // cells below the support 2h (the paper's finer cells, optimisation G-F):
+    // searched by the float64 kernels and the thread-per-particle kernel only
+    if (cell_reach(*p) > 1 && p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_THREAD)
+        return SPH_ERR_INVALID_ARG;
     const bool tensile = p->tensile_eps != 0.0 || p->tensile_pos != 0.0;
     if (tensile && (p->tensile_n < 1 || p->tensile_n > 16 || !(p->dp > 0) ||
                     (p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_WARP)))
@@ -94,6 +105,7 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
     d.nz = dims[2];
     d.ncells = ncells;
     d.euler_every = (int)p.verlet_euler_every;
+    d.reach = cell_reach(p);
     d.clamp = p.clamp_boundary_rho ? 1 : 0;
     d.gamma_is_7 = p.gamma == 7.0;
     d.hf = (float)p.h;

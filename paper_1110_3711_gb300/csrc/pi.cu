@@ -5,7 +5,9 @@
 // evaluate F-F and F-B in one kernel (Section 4.5, optimisation E); boundary
 // targets have their own B-F kernel (continuity only).  Candidates are the
 // particles of the 27 surrounding cells, visited as the 9 x-runs of Fig. 10 /
-// Fig. 11 (cells x-1, x, x+1 of one (y, z) row are contiguous after NL).
+// Fig. 11 (cells x-1, x, x+1 of one (y, z) row are contiguous after NL); with
+// cells of edge in [h, 2h) (the paper's finer cells, optimisation G-F) the 125
+// surrounding cells as 25 x-runs of 5 cells (P.reach = 2).
 //
 // Per ordered pair a <- b with r_ab = x_a - x_b, r = |r_ab| < 2h, q = r/h:
 //   grad_a W_ab = F r_ab,  F = aD/h^2 (-3 + 2.25 q)         (q < 1)
@@ -94,11 +96,12 @@ __device__ __forceinline__ void runs64(const DevParams &P, int self, const doubl
                                        const int32_t *__restrict__ start, Acc64 &o)
 {
     const double s2 = 4.0 * P.h * P.h;
-    int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
-    for (int dz = -1; dz <= 1; ++dz) {
+    const int R = P.reach;
+    int x0 = max(cx - R, 0), x1 = min(cx + R, P.nx - 1);
+    for (int dz = -R; dz <= R; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= P.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             int y = cy + dy;
             if (y < 0 || y >= P.ny) continue;
             int row = P.nx * (y + P.ny * z);
@@ -192,11 +195,12 @@ __device__ __forceinline__ void count_runs(const DevParams &P, double xa, double
                                            unsigned long long &cand, unsigned long long &pairs)
 {
     const double s2 = 4.0 * P.h * P.h;
-    int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
-    for (int dz = -1; dz <= 1; ++dz) {
+    const int R = P.reach;
+    int x0 = max(cx - R, 0), x1 = min(cx + R, P.nx - 1);
+    for (int dz = -R; dz <= R; ++dz) {
         int zz = cz + dz;
         if (zz < 0 || zz >= P.nz) continue;
-        for (int dy = -1; dy <= 1; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
             int yy = cy + dy;
             if (yy < 0 || yy >= P.ny) continue;
             int row = P.nx * (yy + P.ny * zz);

@@ -2,7 +2,9 @@
 // thread per target particle walks its own neighbour ranges and evaluates the
 // pair terms under a per-candidate branch; F-F and F-B in one kernel, B-F in
 // its own (Section 4.5).  Two ways of finding the ranges (Section 4.4):
-//   pi_kernel = 1  the 27 cells from CellBeginEnd inside the kernel (Fig. 11 top)
+//   pi_kernel = 1  the 27 cells from CellBeginEnd inside the kernel (Fig. 11 top);
+//                  with cells of edge in [h, 2h) (optimisation G-F, the paper's
+//                  finer cells) the 125 cells as 25 x-runs of 5 cells
 //   pi_kernel = 2  "FastCells": 9 x-run ranges per cell precomputed after NL by
 //                  k_cell_ranges and read by the kernel (Fig. 11 bottom)
 // Kept as selectable variants of sph_interact so that the paper's GPU
@@ -48,20 +50,22 @@ __device__ __forceinline__ void pair_t(const DevParams &P, const float4 &pa, con
     o.vis = fmaxf(o.vis, fabsf(mu));
 }
 
-// Candidates of one x-run: each gets the shift of its own cell (x-1, x or x+1),
-// found from the first indices of cells x and x+1.
-template <bool MOMENTUM>
+// Candidates of one x-run: each gets the shift of its own cell x + k
+// (k = -R .. R), found from the first indices of cells x - R + 1 .. x + R
+// (cut[0 .. 2R-1]): k = -R + the number of cuts at or below j.
+template <bool MOMENTUM, int R>
 __device__ __forceinline__ void walk_range(const DevParams &P, const float4 &pa, const float4 &va,
-                                           float ca, int j0, int j1, int cut0, int cut1, int dy,
-                                           int dz,
-                                           const float4 *__restrict__ posp,
+                                           float ca, int j0, int j1, const int (&cut)[2 * R],
+                                           int dy, int dz, const float4 *__restrict__ posp,
                                            const float4 *__restrict__ velr, AccT &o)
 {
     const float ya = pa.y - (float)dy * P.sf;
     const float za = pa.z - (float)dz * P.sf;
     for (int j = j0; j < j1; ++j) {
-        // cell x-1 before cut0, cell x before cut1, cell x+1 after
-        const float xa = j < cut0 ? pa.x + P.sf : (j < cut1 ? pa.x : pa.x - P.sf);
+        int k = -R;
+#pragma unroll
+        for (int u = 0; u < 2 * R; ++u) k += j >= cut[u] ? 1 : 0;
+        const float xa = pa.x - (float)k * P.sf;
         float4 pb = posp[j];
         float rx = xa - pb.x, ry = ya - pb.y, rz = za - pb.z;
         float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
@@ -69,10 +73,12 @@ __device__ __forceinline__ void walk_range(const DevParams &P, const float4 &pa,
     }
 }
 
-// The 9 x-runs of one list around cell (cx, cy, cz).  FAST reads the run
-// bounds from the per-cell table (9 x {begin, first of cell x, first of cell
-// x+1, end}); otherwise they come from the cell first indices.
-template <bool MOMENTUM, bool FAST>
+// The (2R+1)^2 x-runs of one list around cell (cx, cy, cz).  FAST (R = 1)
+// reads the run bounds from the per-cell table (9 x {begin, first of cell x,
+// first of cell x+1, end}); otherwise they come from the cell first indices.
+// Cut indices clamp to the row (cells left of x = 0 hold nothing; the first
+// index of cell nx of a row is the end of the row).
+template <bool MOMENTUM, bool FAST, int R>
 __device__ __forceinline__ void runs_t(const DevParams &P, const float4 &pa, const float4 &va,
                                        float ca, uint32_t cell, int cx, int cy, int cz,
                                        const float4 *__restrict__ posp,
@@ -80,27 +86,31 @@ __device__ __forceinline__ void runs_t(const DevParams &P, const float4 &pa, con
                                        const int32_t *__restrict__ start,
                                        const int4 *__restrict__ ranges, AccT &o)
 {
-    for (int q = 0; q < 9; ++q) {
-        const int dz = q / 3 - 1, dy = q % 3 - 1;
-        int4 rg;
+    constexpr int W = 2 * R + 1;
+    for (int q = 0; q < W * W; ++q) {
+        const int dz = q / W - R, dy = q % W - R;
+        int j0, j1, cut[2 * R];
         if (FAST) {
-            rg = ranges[(size_t)cell * 9 + q];
+            const int4 rg = ranges[(size_t)cell * 9 + q];
+            j0 = rg.x;
+            cut[0] = rg.y;
+            cut[2 * R - 1] = rg.z;
+            j1 = rg.w;
         } else {
             const int y = cy + dy, z = cz + dz;
             if (y < 0 || y >= P.ny || z < 0 || z >= P.nz) continue;
             const int row = P.nx * (y + P.ny * z);
-            rg = make_int4(start[row + max(cx - 1, 0)], start[row + cx], start[row + cx + 1],
-                           start[row + min(cx + 1, P.nx - 1) + 1]);
+            j0 = start[row + max(cx - R, 0)];
+            j1 = start[row + min(cx + R, P.nx - 1) + 1];
+#pragma unroll
+            for (int u = 0; u < 2 * R; ++u) cut[u] = start[row + min(max(cx - R + 1 + u, 0), P.nx)];
         }
-        if (rg.x >= rg.w) continue;
-        // a candidate before the first index of cell x lies in cell x-1, one at
-        // or after the first index of cell x+1 in cell x+1 (at the grid edges
-        // the run simply has no such candidates)
-        walk_range<MOMENTUM>(P, pa, va, ca, rg.x, rg.w, rg.y, rg.z, dy, dz, posp, velr, o);
+        if (j0 >= j1) continue;
+        walk_range<MOMENTUM, R>(P, pa, va, ca, j0, j1, cut, dy, dz, posp, velr, o);
     }
 }
 
-template <bool FAST>
+template <bool FAST, int R>
 __global__ void __launch_bounds__(128)
 k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
                   const float4 *__restrict__ velr, const uint32_t *__restrict__ cell,
@@ -122,8 +132,8 @@ k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
         const float ra = va.w * P.inv_rho0f;
         const float ca = P.c0f * ra * ra * ra;
         AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        runs_t<true, FAST>(P, pa, va, ca, c, cx, cy, cz, posp, velr, fstart, franges, o);
-        runs_t<true, FAST>(P, pa, va, ca, c, cx, cy, cz, bposp, bvelr, bstart, branges, o);
+        runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, posp, velr, fstart, franges, o);
+        runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, bposp, bvelr, bstart, branges, o);
         const float ax = fmaf(P.massf, o.ax, P.gf[0]);
         const float ay = fmaf(P.massf, o.ay, P.gf[1]);
         const float az = fmaf(P.massf, o.az, P.gf[2]);
@@ -136,7 +146,7 @@ k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
     block_max_to(&sc->mx.visc, vis, red);
 }
 
-template <bool FAST>
+template <bool FAST, int R>
 __global__ void __launch_bounds__(128)
 k_pi_thread_boundary(int nb, DevParams P, const float4 *__restrict__ bposp,
                      const float4 *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
@@ -155,7 +165,7 @@ k_pi_thread_boundary(int nb, DevParams P, const float4 *__restrict__ bposp,
         const int cx = (int)(c - t * (uint32_t)P.nx), cy = (int)(t % (uint32_t)P.ny),
                   cz = (int)(t / (uint32_t)P.ny);
         AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        runs_t<false, FAST>(P, pa, va, 0.f, c, cx, cy, cz, posp, velr, fstart, franges, o);
+        runs_t<false, FAST, R>(P, pa, va, 0.f, c, cx, cy, cz, posp, velr, fstart, franges, o);
         bar[i] = P.massf * o.ar;
         vis = (double)o.vis;
     }
@@ -205,24 +215,34 @@ int pi32_thread_launch(sph_ctx *ctx)
     }
     if (nf > 0) {
         if (fast)
-            SPH_LAUNCH(ctx, k_pi_thread_fluid<true>, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
+            SPH_LAUNCH(ctx, (k_pi_thread_fluid<true, 1>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
                        (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart, w.franges,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, w.branges,
                        (float4 *)w.acc, w.sc);
+        else if (ctx->dp.reach == 1)
+            SPH_LAUNCH(ctx, (k_pi_thread_fluid<false, 1>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
+                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
+                       (const int4 *)nullptr, (const float4 *)w.bposp, (const float4 *)w.bvelr,
+                       w.bstart, (const int4 *)nullptr, (float4 *)w.acc, w.sc);
         else
-            SPH_LAUNCH(ctx, k_pi_thread_fluid<false>, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
+            SPH_LAUNCH(ctx, (k_pi_thread_fluid<false, 2>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
                        (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
                        (const int4 *)nullptr, (const float4 *)w.bposp, (const float4 *)w.bvelr,
                        w.bstart, (const int4 *)nullptr, (float4 *)w.acc, w.sc);
     }
     if (nb > 0) {
         if (fast)
-            SPH_LAUNCH(ctx, k_pi_thread_boundary<true>, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
+            SPH_LAUNCH(ctx, (k_pi_thread_boundary<true, 1>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
                        (const float4 *)w.posp, (const float4 *)w.velr, w.fstart, w.franges,
                        (float *)w.bar, w.sc);
+        else if (ctx->dp.reach == 1)
+            SPH_LAUNCH(ctx, (k_pi_thread_boundary<false, 1>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
+                       (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
+                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
+                       (const int4 *)nullptr, (float *)w.bar, w.sc);
         else
-            SPH_LAUNCH(ctx, k_pi_thread_boundary<false>, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
+            SPH_LAUNCH(ctx, (k_pi_thread_boundary<false, 2>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
                        (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
                        (const int4 *)nullptr, (float *)w.bar, w.sc);

@@ -47,6 +47,7 @@ struct DevParams {
     int nx, ny, nz;
     uint32_t ncells;
     int euler_every;
+    int reach;            // cells searched on each side: 1 (cell >= 2h) or 2 (h <= cell < 2h)
     int clamp;
     int gamma_is_7;
     int tensile;          // tensile correction on

@@ -54,6 +54,21 @@ def test_error_strings_and_workspace_on_cpu(libsph):
     g5 = sph.make_params(c.params, "fp64")
     g5.gamma = 5.0
     assert sph.sph_workspace_bytes(g5, c.n_f, c.n_b) > 0
+    # cells of edge h (125-cell search): float64 and the thread-per-particle
+    # kernel only; below h the support spans more than two cells
+    for prec, kern, ok in (("fp64", "warp", True), ("fp32", "thread", True),
+                           ("fp32", "warp", False), ("fp32", "thread_fastcells", False)):
+        q = sph.make_params(c.params, prec, kern)
+        q.cell_size = c.params.h
+        if ok:
+            assert sph.sph_workspace_bytes(q, c.n_f, c.n_b) > ws
+        else:
+            with pytest.raises(sph.SphError):
+                sph.sph_workspace_bytes(q, c.n_f, c.n_b)
+    q = sph.make_params(c.params, "fp64")
+    q.cell_size = 0.99 * c.params.h
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(q, c.n_f, c.n_b)
 
 
 def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):

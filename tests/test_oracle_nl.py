@@ -113,3 +113,19 @@ def test_nine_x_runs_equal_27_cells(oracle_lib):
                 k1 = x1 + nx * (y + ny * z)
                 via9.extend(order[start[k0]:start[k1 + 1]].tolist())
         assert via27 == via9
+
+
+def test_search_refuses_cells_below_support(oracle_lib):
+    """The oracle visits the 27 cells around a particle, which hold its support
+    only for cells of edge >= 2h; a finer grid is refused rather than searched
+    incompletely (its cell lists stay available)."""
+    import dataclasses
+    c = random_cloud(200, box=0.1, dp=0.01, n_b=20, seed=4)
+    p = dataclasses.replace(c.params, cell_size=c.params.h)
+    with pytest.raises(ValueError):
+        oracle_lib.pairs(p, c.n_f, c.n_b, c.pos)
+    with pytest.raises(ValueError):
+        oracle_lib.interact(p, c.n_f, c.n_b, c.pos, c.vel, c.rho)
+    cell = oracle_lib.cells(p, c.pos)
+    order, start = oracle_lib.cell_list(p, cell)
+    assert np.array_equal(np.sort(order), np.arange(c.n))
