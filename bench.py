@@ -163,7 +163,7 @@ def barrier(world):
 
 def fine_cells(case):
     """The same case on cells of edge h (half the support), the paper's finer
-    cells (optimisation G-F)."""
+    cells (Section 4.6, optimisation F; Section 3.2 on the CPU)."""
     p = dataclasses.replace(case.params, cell_size=case.params.h)
     return type(case)(**{**case.__dict__, "params": p})
 
@@ -469,7 +469,7 @@ def main():
     if args.ablation_steps > 0:
         # the paper's GPU design on the same workload (Section 4, Fig. 11): one
         # thread per particle, ranges from CellBeginEnd or precomputed per cell,
-        # and the same on cells of edge h (optimisation G-F, 125-cell search);
+        # and the same on cells of edge h (Section 4.6, optimisation F: 125-cell search);
         # all designs over the same steps from the initial state
         abl = {"steps": args.ablation_steps}
         fine = fine_cells(case)

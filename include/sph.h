@@ -81,7 +81,11 @@ extern "C" {
 typedef struct sph_params {
     double dp;            /* particle spacing (m) */
     double h;             /* smoothing length (m); support radius 2h */
-    double cell_size;     /* cell edge (m), normally 2h */
+    double cell_size;     /* cell edge (m): >= 2h searches the 27 surrounding cells (9
+                             x-runs, Fig. 10); an edge in [h, 2h) the 125 surrounding
+                             cells (25 x-runs; the finer cells of Section 4.6,
+                             optimisation F), supported by SPH_FP64 and by
+                             SPH_PI_THREAD only; below h: SPH_ERR_INVALID_ARG */
     double rho0;          /* reference density (kg/m^3) */
     double gamma;         /* Tait exponent (SPH_FP32_SPLIT: 7 only, as in Table 1;
                              other values give SPH_ERR_INVALID_ARG) */

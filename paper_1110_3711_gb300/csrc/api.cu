@@ -47,7 +47,7 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
     // the float32 PI kernels take the sound speed as c0 (rho / rho0)^3, the
     // Tait form of gamma = 7 (Table 1)
     if (p->precision == SPH_FP32_SPLIT && p->gamma != 7.0) return SPH_ERR_INVALID_ARG;
-    // cells below the support 2h (the paper's finer cells, optimisation G-F):
+    // cells below the support 2h (the paper's finer cells, Section 4.6, optimisation F):
     // searched by the float64 kernels and the thread-per-particle kernel only
     if (cell_reach(*p) > 1 && p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_THREAD)
         return SPH_ERR_INVALID_ARG;

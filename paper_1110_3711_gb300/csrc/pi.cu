@@ -6,7 +6,7 @@
 // targets have their own B-F kernel (continuity only).  Candidates are the
 // particles of the 27 surrounding cells, visited as the 9 x-runs of Fig. 10 /
 // Fig. 11 (cells x-1, x, x+1 of one (y, z) row are contiguous after NL); with
-// cells of edge in [h, 2h) (the paper's finer cells, optimisation G-F) the 125
+// cells of edge in [h, 2h) (the paper's finer cells, Section 4.6, optimisation F) the 125
 // surrounding cells as 25 x-runs of 5 cells (P.reach = 2).
 //
 // Per ordered pair a <- b with r_ab = x_a - x_b, r = |r_ab| < 2h, q = r/h:

@@ -3,7 +3,7 @@
 // pair terms under a per-candidate branch; F-F and F-B in one kernel, B-F in
 // its own (Section 4.5).  Two ways of finding the ranges (Section 4.4):
 //   pi_kernel = 1  the 27 cells from CellBeginEnd inside the kernel (Fig. 11 top);
-//                  with cells of edge in [h, 2h) (optimisation G-F, the paper's
+//                  with cells of edge in [h, 2h) (Section 4.6, optimisation F; the paper's
 //                  finer cells) the 125 cells as 25 x-runs of 5 cells
 //   pi_kernel = 2  "FastCells": 9 x-run ranges per cell precomputed after NL by
 //                  k_cell_ranges and read by the kernel (Fig. 11 bottom)

@@ -1,4 +1,4 @@
-"""Cells finer than the support (the paper's finer cells, optimisation G-F):
+"""Cells finer than the support (the paper's finer cells, Section 4.6, optimisation F):
 with cell edge h, or any edge in [h, 2h), a particle's support 2h spans two
 cells on each side, so the search visits 125 cells as 25 x-runs of 5 cells.
 
