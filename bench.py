@@ -473,7 +473,8 @@ def main():
         # all designs over the same steps from the initial state
         abl = {"steps": args.ablation_steps}
         fine = fine_cells(case)
-        for name, kname, cs in (("warp", "warp", case), ("thread", "thread", case),
+        for name, kname, cs in (("warp", "warp", case), ("warp_sym", "warp_sym", case),
+                                ("thread", "thread", case),
                                 ("thread_fastcells", "thread_fastcells", case),
                                 ("thread_hcells", "thread", fine)):
             s_a, r_a = run_form(torch, cs, "fp32", args.ablation_steps, 3, flush, world,

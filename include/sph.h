@@ -60,6 +60,13 @@ extern "C" {
                                        cells from CellBeginEnd (Section 4.4, Fig. 11 top) */
 #define SPH_PI_THREAD_FASTCELLS  2  /* one thread per particle, 9 ranges per cell
                                        precomputed after NL (Fig. 11 bottom) */
+#define SPH_PI_WARP_SYM          3  /* the warp design with symmetric pairs (Section
+                                       3.1, optimisation A, taken to the GPU): pairs
+                                       between different cells evaluated once for
+                                       both particles, both sides added with float
+                                       atomics, so results are not bit-reproducible
+                                       from run to run (float32 rounding only);
+                                       cells >= 2h, no tensile correction */
 
 /* return codes */
 #define SPH_OK                 0

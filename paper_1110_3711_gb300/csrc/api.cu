@@ -42,7 +42,7 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
         !(p->gamma > 0) || !(p->c0 > 0) || !(p->mass > 0) || !(p->cfl > 0) ||
         !(p->alpha >= 0) || !(p->eta2_coef > 0) || p->verlet_euler_every < 1 ||
         (p->precision != SPH_FP64 && p->precision != SPH_FP32_SPLIT) ||
-        p->pi_kernel < SPH_PI_WARP || p->pi_kernel > SPH_PI_THREAD_FASTCELLS)
+        p->pi_kernel < SPH_PI_WARP || p->pi_kernel > SPH_PI_WARP_SYM)
         return SPH_ERR_INVALID_ARG;
     // the float32 PI kernels take the sound speed as c0 (rho / rho0)^3, the
     // Tait form of gamma = 7 (Table 1)
@@ -441,7 +441,8 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b, const double *pos,
     cudaGetDevice(&ctx->device);
     plan_workspace(*p, n_f, n_b, dims, &nc, &ctx->w, (char *)workspace);
     rc = check_cuda(cudaMemsetAsync(ctx->w.sc, 0, sizeof(Scalars), ctx->stream));
-    if (!rc && ctx->precision == SPH_FP32_SPLIT) rc = pi32_setup(ctx);
+    if (!rc && ctx->precision == SPH_FP32_SPLIT)
+        rc = p->pi_kernel == SPH_PI_WARP_SYM ? pi32_sym_setup(ctx) : pi32_setup(ctx);
     if (!rc) rc = load_state(ctx, pos, vel, rho, nullptr, nullptr);
     if (rc) {
         free(ctx);

@@ -255,6 +255,7 @@ int pi_launch(sph_ctx *ctx)
     const int T = 128;
     if (ctx->precision == SPH_FP32_SPLIT) {
         if (ctx->prm.pi_kernel == SPH_PI_WARP) return pi32_launch(ctx);
+        if (ctx->prm.pi_kernel == SPH_PI_WARP_SYM) return pi32_sym_launch(ctx);
         return pi32_thread_launch(ctx);
     } else {
         if (nf > 0)

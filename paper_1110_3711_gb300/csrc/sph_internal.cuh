@@ -155,6 +155,8 @@ int pi_launch(sph_ctx *ctx);
 int pi32_launch(sph_ctx *ctx);
 int pi32_thread_launch(sph_ctx *ctx);
 int pi32_setup(sph_ctx *ctx);
+int pi32_sym_launch(sph_ctx *ctx);
+int pi32_sym_setup(sph_ctx *ctx);
 int boundary_items_launch(sph_ctx *ctx);
 int count_work_launch(sph_ctx *ctx);
 constexpr int kCtrWords = 4;     // work-item counters after the cell counts

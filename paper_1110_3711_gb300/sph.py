@@ -18,7 +18,7 @@ from . import build as _build
 
 SPH_FP64 = 0
 SPH_FP32_SPLIT = 1
-PI_KERNELS = {"warp": 0, "thread": 1, "thread_fastcells": 2}
+PI_KERNELS = {"warp": 0, "thread": 1, "thread_fastcells": 2, "warp_sym": 3}
 FLAG_OUT_OF_GRID = 1
 FLAG_NAN = 2
 FLAG_DT_TOO_SMALL = 4

@@ -65,6 +65,16 @@ def test_error_strings_and_workspace_on_cpu(libsph):
         else:
             with pytest.raises(sph.SphError):
                 sph.sph_workspace_bytes(q, c.n_f, c.n_b)
+    # the symmetric warp kernel: cells >= 2h and no tensile correction
+    q = sph.make_params(c.params, "fp32", "warp_sym")
+    assert sph.sph_workspace_bytes(q, c.n_f, c.n_b) == ws
+    q.cell_size = c.params.h
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(q, c.n_f, c.n_b)
+    q = sph.make_params(c.params, "fp32", "warp_sym")
+    q.tensile_eps, q.tensile_pos = 0.2, 0.01
+    with pytest.raises(sph.SphError):
+        sph.sph_workspace_bytes(q, c.n_f, c.n_b)
     q = sph.make_params(c.params, "fp64")
     q.cell_size = 0.99 * c.params.h
     with pytest.raises(sph.SphError):

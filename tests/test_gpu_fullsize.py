@@ -56,9 +56,10 @@ def test_neighbour_list_bit_exact_full_size(torch_mod, O, dp):
         assert np.array_equal(got, counts)
 
 
-def test_pi_fp32_all_particles_1m(torch_mod, O):
+@pytest.mark.parametrize("pi_kernel", ["warp", "warp_sym"])
+def test_pi_fp32_all_particles_1m(torch_mod, O, pi_kernel):
     c = _perturbed(dam_break(0.005), 1)
-    sim = make_sim(c, "fp32")
+    sim = make_sim(c, "fp32", pi_kernel=pi_kernel)
     sim.neighbour_list()
     sim.interact()
     ace, ar, mx = sim.forces()

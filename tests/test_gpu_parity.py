@@ -144,7 +144,7 @@ def test_pi_fp64_matches_oracle(torch_mod, O, case_fn):
     assert mx[1] == pytest.approx(max(O.sound(c.params, r) for r in rho), rel=1e-13)
 
 
-@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "thread_fastcells"])
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "thread_fastcells", "warp_sym"])
 def test_pi_fp32_split_matches_oracle(torch_mod, O, pi_kernel):
     """float32 PI on cell-relative offsets, every PI kernel design: errors
     relative to the force scale (|g| + max|ace|) within 2e-5 and density rates
@@ -186,7 +186,7 @@ def test_fp64_time_loop_matches_oracle(torch_mod, O):
     assert nsteps == steps and tt == pytest.approx(t, rel=1e-12)
 
 
-@pytest.mark.parametrize("pi_kernel", ["warp", "thread_fastcells"])
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread_fastcells", "warp_sym"])
 def test_fp32_split_time_loop_error_budget(torch_mod, O, pi_kernel):
     """SPH_FP32_SPLIT against the FP64 oracle after 100 steps."""
     c = dam_break(0.02)
