@@ -314,6 +314,33 @@ __global__ void k_export_forces(int nf, int nb, size_t N, uint32_t ncells, const
     }
 }
 
+// Boundary particles whose staged position differs, bit for bit, from the one
+// the current boundary list holds set sc->bmoved.
+__global__ void k_boundary_same(int nb, const double *__restrict__ stage, const double *bx,
+                                const double *by, const double *bz, const uint32_t *bid,
+                                Scalars *sc)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const size_t g = bid[i];
+    const bool same = __double_as_longlong(stage[3 * g]) == __double_as_longlong(bx[i]) &&
+                      __double_as_longlong(stage[3 * g + 1]) == __double_as_longlong(by[i]) &&
+                      __double_as_longlong(stage[3 * g + 2]) == __double_as_longlong(bz[i]);
+    if (!same) sc->bmoved = 1u;
+}
+
+// Densities of the boundary particles from the staged state (list unchanged).
+template <typename Real>
+__global__ void k_boundary_rho(int nb, size_t N, const double *__restrict__ stage,
+                               const uint32_t *__restrict__ bid, Real *brho, Real *brhom)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nb) return;
+    const size_t g = bid[i];
+    brho[i] = (Real)stage[6 * N + g];
+    brhom[i] = (Real)stage[10 * N + g];
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -374,11 +401,39 @@ int load_state(sph_ctx *ctx, const double *pos, const double *vel, const double 
     int rc = stage_in(ctx, pos, vel, rho, velm, rhom);
     if (rc) return rc;
     ctx->cur = 0;
-    ctx->branges_ready = false;
     if (ctx->precision == SPH_FP32_SPLIT) launch_scatter_in<float>(ctx, 0);
     else launch_scatter_in<double>(ctx, 0);
-    rc = nl_boundary_build(ctx);
-    if (rc) return rc;
+    Workspace &w = ctx->w;
+    const int nb = (int)ctx->nb, T = 256;
+    const size_t N = (size_t)(ctx->nf + ctx->nb);
+    // Boundaries never move: when the new state keeps every boundary position,
+    // the boundary list stands and only the densities are taken over.
+    bool rebuild = !ctx->boundary_built;
+    if (!rebuild && nb > 0) {
+        uint32_t moved = 0;
+        if (check_cuda(cudaMemsetAsync(&w.sc->bmoved, 0, sizeof(uint32_t), ctx->stream)))
+            return SPH_ERR_CUDA;
+        SPH_LAUNCH(ctx, k_boundary_same, (nb + T - 1) / T, T, 0, ctx->stream, nb, w.stage, w.bx,
+                   w.by, w.bz, w.bid, w.sc);
+        if (check_cuda(cudaMemcpyAsync(&moved, &w.sc->bmoved, sizeof(uint32_t),
+                                       cudaMemcpyDeviceToHost, ctx->stream)) ||
+            check_cuda(cudaStreamSynchronize(ctx->stream)))
+            return SPH_ERR_CUDA;
+        rebuild = moved != 0;
+    }
+    if (rebuild) {
+        ctx->branges_ready = false;
+        rc = nl_boundary_build(ctx);
+        if (rc) return rc;
+        ctx->boundary_built = true;
+    } else if (nb > 0) {
+        if (ctx->precision == SPH_FP32_SPLIT)
+            SPH_LAUNCH(ctx, k_boundary_rho<float>, (nb + T - 1) / T, T, 0, ctx->stream, nb, N,
+                       w.stage, w.bid, (float *)w.brho, (float *)w.brhom);
+        else
+            SPH_LAUNCH(ctx, k_boundary_rho<double>, (nb + T - 1) / T, T, 0, ctx->stream, nb, N,
+                       w.stage, w.bid, (double *)w.brho, (double *)w.brhom);
+    }
     ctx->nl_valid = ctx->pi_valid = false;
     return check_cuda(cudaStreamSynchronize(ctx->stream));
 }

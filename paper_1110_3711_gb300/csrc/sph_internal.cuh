@@ -35,7 +35,7 @@ struct Scalars {
     double time;
     long long step;     // completed steps
     uint32_t flags;
-    uint32_t pad;
+    uint32_t bmoved;    // set when a staged boundary position differs from the list's
 };
 
 // Constants every kernel needs, passed by value.
@@ -121,6 +121,7 @@ struct sph_ctx {
     int device;
     int pi_grid_f, pi_grid_b;   // persistent grid sizes of the FP32 PI kernels
     bool branges_ready;         // boundary x-run table built for the current boundary list
+    bool boundary_built;        // the boundary list exists (built at least once)
     // sph_run_graph: executable graphs of two consecutive steps, one per value
     // of `cur` at the start, and the number of kernels each launches
     cudaGraphExec_t graph[2];

@@ -107,6 +107,34 @@ def test_nl_cell_faces_bit_exact(torch_mod, O, precision):
     sim.status(clear=True)
 
 
+@pytest.mark.parametrize("change", ["boundary_moved", "boundary_density"])
+def test_set_state_takes_the_boundary_over(torch_mod, O, change):
+    """sph_set_state with moved boundary particles rebuilds the boundary list;
+    with unmoved ones it keeps the list and takes the new densities.  Either
+    way PI equals that of a context created from the same state."""
+    c = dam_break(0.02)
+    sim = make_sim(c, "fp64")
+    sim.step()
+    pos, vel, rho = sim.get_state()
+    if change == "boundary_moved":
+        pos[c.n_f:] += np.array([0.4, 0.3, 0.0]) * c.params.dp
+    else:
+        rho[c.n_f:] = 1000.0 + np.linspace(0.0, 5.0, c.n_b)
+    sim.set_state(pos, vel, rho)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, _ = sim.forces()
+    c2 = type(c)(**{**c.__dict__, "pos": pos, "vel": vel, "rho": rho})
+    fresh = make_sim(c2, "fp64")
+    fresh.neighbour_list()
+    fresh.interact()
+    ace2, ar2, _ = fresh.forces()
+    assert np.array_equal(ace, ace2) and np.array_equal(ar, ar2)
+    oace, oar, _, _, _ = O.interact(c.params, c.n_f, c.n_b, pos, vel, rho)
+    assert np.abs(ace - oace).max() <= 1e-12 * np.abs(oace).max()
+    assert np.abs(ar - oar).max() <= 1e-12 * np.abs(oar).max()
+
+
 def test_work_counts_exact(torch_mod, O):
     c = dam_break(0.02)
     sim = make_sim(c, "fp32")
