@@ -218,6 +218,7 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
         W.branges = b.take<int4>((size_t)*ncells * 9);
     }
     W.fstart = b.take<int32_t>((size_t)*ncells + 2);
+    W.origin = b.take<double>((size_t)dims[0] + dims[1] + dims[2]);
     W.bstart = b.take<int32_t>((size_t)*ncells + 2);
     int64_t hist = (int64_t)256 * radix_tiles(m > 0 ? m : 1);
     W.radix_hist = b.take<uint32_t>((size_t)hist);
@@ -496,6 +497,7 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b, const double *pos,
     cudaGetDevice(&ctx->device);
     plan_workspace(*p, n_f, n_b, dims, &nc, &ctx->w, (char *)workspace);
     rc = check_cuda(cudaMemsetAsync(ctx->w.sc, 0, sizeof(Scalars), ctx->stream));
+    if (!rc) rc = fill_origins(ctx);
     if (!rc && ctx->precision == SPH_FP32_SPLIT)
         rc = p->pi_kernel == SPH_PI_WARP_SYM ? pi32_sym_setup(ctx) : pi32_setup(ctx);
     if (!rc) rc = load_state(ctx, pos, vel, rho, nullptr, nullptr);

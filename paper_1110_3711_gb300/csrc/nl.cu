@@ -359,16 +359,33 @@ __device__ __forceinline__ void eos32(const DevParams &P, float rho, float *pr, 
     *c = P.c0f * cs;
 }
 
-__device__ __forceinline__ void cell_origin(const DevParams &P, uint32_t c, double *ox, double *oy,
-                                            double *oz)
+// Origin of every cell column along each axis, min_d + c s, written once per
+// context so that the per-step kernels do not spend the float64 unit on it.
+__global__ void k_fill_origins(DevParams P, double *origin)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < P.nx) origin[k] = P.dom_min[0] + (double)k * P.s;
+    else if (k < P.nx + P.ny) origin[k] = P.dom_min[1] + (double)(k - P.nx) * P.s;
+    else if (k < P.nx + P.ny + P.nz) origin[k] = P.dom_min[2] + (double)(k - P.nx - P.ny) * P.s;
+}
+
+int fill_origins(sph_ctx *ctx)
+{
+    const int n = ctx->dp.nx + ctx->dp.ny + ctx->dp.nz, T = 256;
+    SPH_LAUNCH(ctx, k_fill_origins, (n + T - 1) / T, T, 0, ctx->stream, ctx->dp, ctx->w.origin);
+    return check_cuda(cudaGetLastError());
+}
+
+__device__ __forceinline__ void cell_origin(const DevParams &P, const double *__restrict__ origin,
+                                            uint32_t c, double *ox, double *oy, double *oz)
 {
     uint32_t cx = c % (uint32_t)P.nx;
     uint32_t t = c / (uint32_t)P.nx;
     uint32_t cy = t % (uint32_t)P.ny;
     uint32_t cz = t / (uint32_t)P.ny;
-    *ox = P.dom_min[0] + (double)cx * P.s;
-    *oy = P.dom_min[1] + (double)cy * P.s;
-    *oz = P.dom_min[2] + (double)cz * P.s;
+    *ox = origin[cx];
+    *oy = origin[P.nx + cy];
+    *oz = origin[P.nx + P.ny + cz];
 }
 
 // Threads [0, nf): gather fluid arrays from buffer `src` to buffer `dst` in the
@@ -391,12 +408,15 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
           uint32_t *__restrict__ cell, const Real *__restrict__ brho,
           typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
           const int32_t *__restrict__ bstart, const int32_t *__restrict__ fstart,
-          uint32_t *__restrict__ items, uint32_t *__restrict__ ctr, Scalars *sc)
+          uint32_t *__restrict__ items, uint32_t *__restrict__ ctr,
+          const double *__restrict__ origin, Scalars *sc)
 {
     __shared__ double red[32];
+    __shared__ float redf[32];
     typedef typename Vec4<Real>::T V4;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
-    double cmax = 0.0;
+    // the largest sound speed, in the precision of the form
+    Real cmax = 0;
     bool item = false;
     if (i < nf) {
         uint32_t s = val_sorted[i];
@@ -417,14 +437,14 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
             float pr, cs;
             eos32(P, (float)rho, &pr, &cs);
             double ox = 0.0, oy = 0.0, oz = 0.0;
-            if (c < P.ncells) cell_origin(P, c, &ox, &oy, &oz);
+            if (c < P.ncells) cell_origin(P, origin, c, &ox, &oy, &oz);
             pp.x = (Real)(x - ox); pp.y = (Real)(y - oy); pp.z = (Real)(z - oz); pp.w = (Real)pr;
-            if (c < P.ncells) cmax = (double)cs;
+            if (c < P.ncells) cmax = (Real)cs;
         } else {
             double pr, cs;
             eos64(P, (double)rho, &pr, &cs);
             pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z; pp.w = (Real)pr;
-            if (c < P.ncells) cmax = cs;
+            if (c < P.ncells) cmax = (Real)cs;
         }
         vv.x = vx; vv.y = vy; vv.z = vz; vv.w = rho;
         posp[i] = pp;
@@ -440,12 +460,12 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
                 float pr, cs;
                 eos32(P, (float)rho, &pr, &cs);
                 pp.w = (Real)pr;
-                cmax = (double)cs;
+                cmax = (Real)cs;
             } else {
                 double pr, cs;
                 eos64(P, (double)rho, &pr, &cs);
                 pp.w = (Real)pr;
-                cmax = cs;
+                cmax = (Real)cs;
             }
             bposp[j] = pp;
             bvelr[j] = vv;
@@ -462,7 +482,8 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
             if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
         }
     }
-    block_max_to(&sc->mx.c, cmax, red);
+    if (SPLIT) block_max_to_f(&sc->mx.c, (float)cmax, redf);
+    else block_max_to(&sc->mx.c, (double)cmax, red);
 }
 
 // Boundary list (built once): gather the id-ordered boundary state staged in
@@ -475,7 +496,8 @@ __global__ void k_boundary_place(int nb, uint32_t nf, DevParams P,
                                  const double *__restrict__ in_rhom,
                                  double *bx, double *by, double *bz, Real *brho, Real *brhom,
                                  uint32_t *bid, uint32_t *bcell,
-                                 typename Vec4<Real>::T *bposp, typename Vec4<Real>::T *bvelr)
+                                 typename Vec4<Real>::T *bposp, typename Vec4<Real>::T *bvelr,
+                                 const double *__restrict__ origin)
 {
     typedef typename Vec4<Real>::T V4;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -492,7 +514,7 @@ __global__ void k_boundary_place(int nb, uint32_t nf, DevParams P,
     V4 pp, vv;
     if (SPLIT) {
         double ox = 0.0, oy = 0.0, oz = 0.0;
-        if (c < P.ncells) cell_origin(P, c, &ox, &oy, &oz);
+        if (c < P.ncells) cell_origin(P, origin, c, &ox, &oy, &oz);
         pp.x = (Real)(x - ox); pp.y = (Real)(y - oy); pp.z = (Real)(z - oz);
     } else {
         pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z;
@@ -557,7 +579,8 @@ static int nl_fluid_t(sph_ctx *ctx)
                    (Real *)w.vmy[dst], (Real *)w.vmz[dst], (Real *)w.rho[dst], (Real *)w.rhom[dst],
                    w.id[dst], (typename Vec4<Real>::T *)w.posp, (typename Vec4<Real>::T *)w.velr,
                    w.cell, (const Real *)w.brho, (typename Vec4<Real>::T *)w.bposp,
-                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.fstart, w.items_f, w.ctr, w.sc);
+                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.fstart, w.items_f, w.ctr,
+                   w.origin, w.sc);
     }
     ctx->cur = dst;
     return check_cuda(cudaGetLastError());
@@ -593,7 +616,7 @@ static int nl_boundary_t(sph_ctx *ctx)
         SPH_LAUNCH(ctx, (k_boundary_place<Real, SPLIT>), (nb + T - 1) / T, T, 0, st, nb,
                    (uint32_t)nf, ctx->dp, w.key_sorted, w.val_sorted, in_pos, in_rho, in_rhom,
                    w.bx, w.by, w.bz, (Real *)w.brho, (Real *)w.brhom, w.bid, w.bcell,
-                   (typename Vec4<Real>::T *)w.bposp, (typename Vec4<Real>::T *)w.bvelr);
+                   (typename Vec4<Real>::T *)w.bposp, (typename Vec4<Real>::T *)w.bvelr, w.origin);
     }
     int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.bstart, (int64_t)ctx->ncells + 2,
                                 w.scan_part, st);

@@ -90,6 +90,7 @@ struct Workspace {
     uint32_t *items_f, *items_b;  // PI work items: first target index of a (cell, 32-target chunk)
     int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
     int32_t *fstart, *bstart; // [ncells + 2]
+    double *origin;           // cell origins min_d + c s along x (nx), y (ny), z (nz)
     uint32_t *radix_hist;     // [256 * tiles]
     uint32_t *scan_part;      // scan partials
     // adjoint scratch (SPH_FP64 contexts): cotangents of F and D, the adjoint
@@ -156,6 +157,7 @@ int pi_launch(sph_ctx *ctx);
 int pi32_launch(sph_ctx *ctx);
 int pi32_thread_launch(sph_ctx *ctx);
 int pi32_setup(sph_ctx *ctx);
+int fill_origins(sph_ctx *ctx);
 int pi32_sym_launch(sph_ctx *ctx);
 int pi32_sym_setup(sph_ctx *ctx);
 int boundary_items_launch(sph_ctx *ctx);
@@ -196,6 +198,26 @@ __device__ __forceinline__ float warp_maxf(float v)
 {
     for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
+}
+
+// Block-wide max of a non-negative float, one atomic per block (the float64
+// unit is used once per block).
+__device__ __forceinline__ void block_max_to_f(unsigned long long *dst, float v, float *smem32)
+{
+    bool nan = v != v;
+    unsigned anynan = __syncthreads_or(nan);
+    float m = warp_maxf(nan ? 0.0f : v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) smem32[wid] = m;
+    __syncthreads();
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        float t = lane < nw ? smem32[lane] : 0.0f;
+        t = warp_maxf(t);
+        if (lane == 0)
+            atomic_max_nonneg(dst, anynan ? __longlong_as_double(0x7ff8000000000000LL) : (double)t);
+    }
+    __syncthreads();
 }
 
 // Block-wide max of a non-negative value followed by one atomic per block.

@@ -29,6 +29,22 @@ __device__ __forceinline__ double step_dt(const DevParams &P, const Scalars *sc)
     return P.cfl * fmin(dtf, dtcv);
 }
 
+// Exact float -> double through the bit pattern (exponent rebiased,
+// significand widened), so the split form's position increments reach the
+// float64 accumulation without a conversion on the float64 unit, the scarce
+// resource of this kernel.  Subnormal floats (below 1.2e-38) become 0; inf
+// and NaN stay inf and NaN.
+__device__ __forceinline__ double widen(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    const uint32_t e = (u >> 23) & 0xffu;
+    const uint32_t sign = u & 0x80000000u;
+    if (e == 0u) return __hiloint2double((int)sign, 0);
+    const uint32_t ex = e == 255u ? 0x7ffu : e + 896u;
+    return __hiloint2double((int)(sign | (ex << 20) | ((u & 0x7fffffu) >> 3)), (int)(u << 29));
+}
+__device__ __forceinline__ double widen(double f) { return f; }
+
 template <typename Real> struct V4T;
 template <> struct V4T<float> { typedef float4 T; };
 template <> struct V4T<double> { typedef double4_32a T; };
@@ -43,16 +59,18 @@ k_su(int nf, int nb, int fblocks, DevParams P, const int32_t *__restrict__ fstar
      Real *__restrict__ rho, Real *__restrict__ rhom, const typename V4T<Real>::T *__restrict__ acc,
      Real *__restrict__ brho, Real *__restrict__ brhom, const Real *__restrict__ bar, Scalars *sc)
 {
-    __shared__ double sdt;
+    // dt and its multiples in the precision of the form, once per block
+    __shared__ Real sdt[3];
     __shared__ int seuler;
     if (threadIdx.x == 0) {
-        sdt = step_dt(P, sc);
+        const double dt = step_dt(P, sc);
+        sdt[0] = (Real)dt;
+        sdt[1] = (Real)(2.0 * dt);
+        sdt[2] = (Real)(0.5 * dt * dt);
         seuler = ((sc->step + 1) % P.euler_every) == 0;
     }
     __syncthreads();
-    const double dt = sdt;
-    const Real dtr = (Real)dt;
-    const Real dt2 = (Real)(2.0 * dt);
+    const Real dtr = sdt[0], dt2 = sdt[1], hdt2 = sdt[2];
     bool nan = false;
     if ((int)blockIdx.x < fblocks) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -61,10 +79,9 @@ k_su(int nf, int nb, int fblocks, DevParams P, const int32_t *__restrict__ fstar
             Real v0 = vx[i], v1 = vy[i], v2 = vz[i];
             // x^{n+1} = x^n + (dt v^n + dt^2/2 F^n): the increment in the precision
             // of the form, the accumulation always in float64
-            const Real hdt2 = (Real)(0.5 * dt * dt);
-            x[i] = x[i] + (double)(dtr * v0 + hdt2 * f.x);
-            y[i] = y[i] + (double)(dtr * v1 + hdt2 * f.y);
-            z[i] = z[i] + (double)(dtr * v2 + hdt2 * f.z);
+            x[i] = x[i] + widen(dtr * v0 + hdt2 * f.x);
+            y[i] = y[i] + widen(dtr * v1 + hdt2 * f.y);
+            z[i] = z[i] + widen(dtr * v2 + hdt2 * f.z);
             Real r = rho[i];
             Real nv0, nv1, nv2, nr;
             if (seuler) {
