@@ -192,6 +192,47 @@ def test_pi_fp32_split_matches_oracle(torch_mod, O, pi_kernel):
     assert mx[2] == pytest.approx(ovm, rel=1e-5)
 
 
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "thread_fastcells", "warp_sym"])
+def test_pi_fp32_dense_cells(torch_mod, O, pi_kernel):
+    """Cells holding up to about 110 particles (random cloud, 53 per occupied
+    cell on average): a cell spans several work items of the warp kernels and
+    the own-cell candidates of an item include targets of other items."""
+    c = random_cloud(4000, box=0.1, dp=0.01, n_b=600, seed=21)
+    sim = make_sim(c, "fp32", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(c.params, c.n_f, c.n_b, c.pos, c.vel, c.rho)
+    assert np.abs(ace - oace).max() / (9.81 + np.abs(oace).max()) < 2e-5
+    assert np.abs(ar - oar).max() / np.abs(oar).max() < 2e-5
+    assert mx[2] == pytest.approx(ovm, rel=1e-5)
+
+
+@pytest.mark.parametrize("pi_kernel", ["warp", "warp_sym"])
+def test_pi_fp32_with_particles_outside_the_grid(torch_mod, O, pi_kernel):
+    """Fluid particles outside the cell grid take no part in PI (sentinel cell);
+    every other particle's forces match the oracle's."""
+    c = dam_break(0.02)
+    vel, rho = _random_state(c, 3)
+    pos = c.pos.copy()
+    out = [5, 77, 4000]
+    pos[5] = [-5.0, 0.1, 0.1]
+    pos[77] = [0.2, 0.2, 50.0]
+    pos[4000] = [0.3, -1.0, 0.05]
+    c2 = type(c)(**{**c.__dict__, "pos": pos, "vel": vel, "rho": rho})
+    sim = make_sim(c2, "fp32", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, _ = sim.forces()
+    oace, oar, _, _, nout = O.interact(c.params, c.n_f, c.n_b, pos, vel, rho)
+    assert nout == len(out)
+    keep = np.setdiff1d(np.arange(c.n_f), out)
+    assert np.abs(ace[keep] - oace[keep]).max() / (9.81 + np.abs(oace).max()) < 2e-5
+    assert np.abs(ar - oar)[np.r_[keep, np.arange(c.n_f, c.n)]].max() / np.abs(oar).max() < 2e-5
+    from paper_1110_3711_gb300.sph import FLAG_OUT_OF_GRID
+    assert sim.status(clear=True) & FLAG_OUT_OF_GRID
+
+
 def test_fp64_time_loop_matches_oracle(torch_mod, O):
     """100 steps of the 3D dam break at dp = 0.02 (about 10k fluid particles)."""
     c = dam_break(0.02)
