@@ -36,7 +36,8 @@ if ROOT not in sys.path:
 from sphcases import dam_break  # noqa: E402
 
 # FLOPs of the method per unit of work, counted from the formulas (every add,
-# sub, mul, div, sqrt, compare, abs and max is 1, "Roofline").
+# sub, mul, div, sqrt, compare, abs and max is one FLOP, so a multiply-add is
+# two, as in the FMA peak the fraction is taken against).
 FLOP_PER_CANDIDATE = 9        # r_ab (3), |r_ab|^2 (5), test (1)
 FLOP_PER_PAIR_FLUID = 45      # kernel gradient, viscosity, momentum, continuity, dt term
 FLOP_PER_PAIR_BOUNDARY = 24   # kernel gradient, continuity, dt term

@@ -105,7 +105,8 @@ def test_adjoint_differentiable_configuration(torch_mod):
     400 steps, checkpoints every 20 steps, 64 sensors on the wall behind the
     column, mean over the last 100 states.  Central differences along the
     normalised gradient (no cancellation between components) and in alpha.
-    The C0 viscosity switch limits FD accuracy, hence the
+    The viscosity switch (Pi = 0 for v.r >= 0) is only C0: every pair whose
+    v.r changes sign inside the FD interval adds an O(eps) error, hence the
     per-check bars."""
     torch = torch_mod
     from paper_1110_3711_gb300.autograd import DamBreakRun
