@@ -149,6 +149,42 @@ __device__ __forceinline__ void cell_coords(const DevParams &P, uint32_t c, int 
         }                                                                          \
     }
 
+// FOR_RUNS with the float32 pre-test of the float64 PI (pi.cu): a candidate
+// whose cell-relative float32 offset lies certainly outside the support of the
+// target's offset fa (threshold 4h^2 (1 + 1e-5), above the float32 error of
+// the offsets) is skipped before the body, which keeps its exact float64 test,
+// so the pairs and the results are unchanged.
+#define FOR_RUNS_F(P, cx, cy, cz, start, fa, posf, j, ...)                            \
+    {                                                                                  \
+        const int R_ = (P).reach;                                                      \
+        const float s2f_ = (P).four_h2f * (1.0f + 1e-5f);                              \
+        int x0_ = max((cx) - R_, 0), x1_ = min((cx) + R_, (P).nx - 1);                 \
+        for (int dz_ = -R_; dz_ <= R_; ++dz_) {                                        \
+            int z_ = (cz) + dz_;                                                       \
+            if (z_ < 0 || z_ >= (P).nz) continue;                                      \
+            const float za_ = (fa).z - (float)dz_ * (P).sf;                            \
+            for (int dy_ = -R_; dy_ <= R_; ++dy_) {                                    \
+                int y_ = (cy) + dy_;                                                   \
+                if (y_ < 0 || y_ >= (P).ny) continue;                                  \
+                const float ya_ = (fa).y - (float)dy_ * (P).sf;                        \
+                int row_ = (P).nx * (y_ + (P).ny * z_);                                \
+                int cut_[4];                                                           \
+                for (int u_ = 0; u_ < 2 * R_; ++u_)                                    \
+                    cut_[u_] = (start)[row_ + min(max((cx) - R_ + 1 + u_, 0), (P).nx)]; \
+                int e_ = (start)[row_ + x1_ + 1];                                      \
+                for (int j = (start)[row_ + x0_]; j < e_; ++j) {                       \
+                    int k_ = -R_;                                                      \
+                    for (int u_ = 0; u_ < 2 * R_; ++u_) k_ += j >= cut_[u_] ? 1 : 0;   \
+                    const float4 fb_ = (posf)[j];                                      \
+                    const float ex_ = (fa).x - (float)k_ * (P).sf - fb_.x;             \
+                    const float ey_ = ya_ - fb_.y, ez_ = za_ - fb_.z;                  \
+                    if (!(fmaf(ex_, ex_, fmaf(ey_, ey_, ez_ * ez_)) < s2f_)) continue; \
+                    { __VA_ARGS__ }                                                    \
+                }                                                                      \
+            }                                                                          \
+        }                                                                              \
+    }
+
 // ---- adjoint SU ------------------------------------------------------------
 
 __global__ void k_adj_su_fluid(int nf, size_t N, DevParams P, const int32_t *__restrict__ fstart,
@@ -236,7 +272,8 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
                const int32_t *__restrict__ fstart, const double4_32a *__restrict__ bposp,
                const double4_32a *__restrict__ bvelr, const int32_t *__restrict__ bstart,
                const double *__restrict__ gF, const double *__restrict__ gD,
-               double *__restrict__ lam_s, double *__restrict__ part)
+               double *__restrict__ lam_s, double *__restrict__ part,
+               const float4 *__restrict__ posf, const float4 *__restrict__ bposf)
 {
     __shared__ double red[kAdjThreads / 32];
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -251,8 +288,9 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
         int cx, cy, cz;
         cell_coords(P, cell[i], &cx, &cy, &cz);
         PairGrad g;
+        const float4 fa = posf[i];
         // fluid neighbours: F-F in both directions
-        FOR_RUNS(P, cx, cy, cz, fstart, j, {
+        FOR_RUNS_F(P, cx, cy, cz, fstart, fa, posf, j, {
             if (j == i) continue;
             const double4_32a pb = posp[j];
             const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
@@ -276,7 +314,7 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
             lr += g.rho_b;
         })
         // boundary neighbours: F-B (momentum + continuity) and B-F (continuity)
-        FOR_RUNS(P, cx, cy, cz, bstart, j, {
+        FOR_RUNS_F(P, cx, cy, cz, bstart, fa, bposf, j, {
             const double4_32a pb = bposp[j];
             const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
             const double r2 = rx * rx + ry * ry + rz * rz;
@@ -318,7 +356,8 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
                   const int32_t *__restrict__ bstart, const double4_32a *__restrict__ posp,
                   const double4_32a *__restrict__ velr, const int32_t *__restrict__ fstart,
                   const double *__restrict__ gF, const double *__restrict__ gD,
-                  double *__restrict__ lam_s)
+                  double *__restrict__ lam_s, const float4 *__restrict__ posf,
+                  const float4 *__restrict__ bposf)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nb || j >= bstart[P.ncells]) return;
@@ -329,7 +368,8 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
     cell_coords(P, bcell[j], &cx, &cy, &cz);
     double lr = 0.0;
     PairGrad g;
-    FOR_RUNS(P, cx, cy, cz, fstart, i, {
+    const float4 fb = bposf[j];
+    FOR_RUNS_F(P, cx, cy, cz, fstart, fb, posf, i, {
         const double4_32a pa = posp[i];
         const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
         const double r2 = rx * rx + ry * ry + rz * rz;
@@ -571,12 +611,12 @@ extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *la
         SPH_LAUNCH(ctx, k_adj_pi_fluid, blocks_f, T, 0, st, nf, N, ctx->dp,
                    (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
                    (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
-                   w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part);
+                   w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part, w.posf, w.bposf);
     if (nb > 0 && nf > 0)
         SPH_LAUNCH(ctx, k_adj_pi_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
                    (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
                    (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, w.adj_gF,
-                   w.adj_gD, w.adj_lam);
+                   w.adj_gD, w.adj_lam, w.posf, w.bposf);
     if (N > 0)
         SPH_LAUNCH(ctx, k_adj_out, (unsigned)((N + T - 1) / T), T, 0, st, nf, nb, N, w.id[c],
                    w.bid, w.adj_lam, lam);

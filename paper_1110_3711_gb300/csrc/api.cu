@@ -200,6 +200,10 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.bid = b.take<uint32_t>(nb);
     W.bcell = b.take<uint32_t>(nb);
     W.bposp = b.take<char>(V4 * nb);
+    if (p.precision == SPH_FP64) {
+        W.posf = b.take<float4>(nf > 0 ? nf : 1);
+        W.bposf = b.take<float4>(nb > 0 ? nb : 1);
+    }
     W.bvelr = b.take<char>(V4 * nb);
     W.bar = b.take<char>(R * nb);
     int64_t m = nf > nb ? nf : nb;

@@ -409,7 +409,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
           typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
           const int32_t *__restrict__ bstart, const int32_t *__restrict__ fstart,
           uint32_t *__restrict__ items, uint32_t *__restrict__ ctr,
-          const double *__restrict__ origin, Scalars *sc)
+          const double *__restrict__ origin, float4 *__restrict__ posf, Scalars *sc)
 {
     __shared__ double red[32];
     __shared__ float redf[32];
@@ -444,7 +444,12 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
             double pr, cs;
             eos64(P, (double)rho, &pr, &cs);
             pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z; pp.w = (Real)pr;
-            if (c < P.ncells) cmax = (Real)cs;
+            if (c < P.ncells) {
+                cmax = (Real)cs;
+                double ox, oy, oz;
+                cell_origin(P, origin, c, &ox, &oy, &oz);
+                posf[i] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
+            }
         }
         vv.x = vx; vv.y = vy; vv.z = vz; vv.w = rho;
         posp[i] = pp;
@@ -497,7 +502,7 @@ __global__ void k_boundary_place(int nb, uint32_t nf, DevParams P,
                                  double *bx, double *by, double *bz, Real *brho, Real *brhom,
                                  uint32_t *bid, uint32_t *bcell,
                                  typename Vec4<Real>::T *bposp, typename Vec4<Real>::T *bvelr,
-                                 const double *__restrict__ origin)
+                                 const double *__restrict__ origin, float4 *__restrict__ bposf)
 {
     typedef typename Vec4<Real>::T V4;
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -518,6 +523,11 @@ __global__ void k_boundary_place(int nb, uint32_t nf, DevParams P,
         pp.x = (Real)(x - ox); pp.y = (Real)(y - oy); pp.z = (Real)(z - oz);
     } else {
         pp.x = (Real)x; pp.y = (Real)y; pp.z = (Real)z;
+        if (c < P.ncells) {
+            double ox, oy, oz;
+            cell_origin(P, origin, c, &ox, &oy, &oz);
+            bposf[i] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
+        }
     }
     pp.w = 0;
     vv.x = 0; vv.y = 0; vv.z = 0; vv.w = (Real)in_rho[nf + k];
@@ -580,7 +590,7 @@ static int nl_fluid_t(sph_ctx *ctx)
                    w.id[dst], (typename Vec4<Real>::T *)w.posp, (typename Vec4<Real>::T *)w.velr,
                    w.cell, (const Real *)w.brho, (typename Vec4<Real>::T *)w.bposp,
                    (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.fstart, w.items_f, w.ctr,
-                   w.origin, w.sc);
+                   w.origin, w.posf, w.sc);
     }
     ctx->cur = dst;
     return check_cuda(cudaGetLastError());
@@ -616,7 +626,8 @@ static int nl_boundary_t(sph_ctx *ctx)
         SPH_LAUNCH(ctx, (k_boundary_place<Real, SPLIT>), (nb + T - 1) / T, T, 0, st, nb,
                    (uint32_t)nf, ctx->dp, w.key_sorted, w.val_sorted, in_pos, in_rho, in_rhom,
                    w.bx, w.by, w.bz, (Real *)w.brho, (Real *)w.brhom, w.bid, w.bcell,
-                   (typename Vec4<Real>::T *)w.bposp, (typename Vec4<Real>::T *)w.bvelr, w.origin);
+                   (typename Vec4<Real>::T *)w.bposp, (typename Vec4<Real>::T *)w.bvelr, w.origin,
+                   w.bposf);
     }
     int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.bstart, (int64_t)ctx->ncells + 2,
                                 w.scan_part, st);

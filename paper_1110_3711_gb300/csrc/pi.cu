@@ -88,26 +88,47 @@ __device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa
     o.vis = fmax(o.vis, fabs(mu));
 }
 
+// The candidates of the (2R+1)^2 x-runs around cell (cx, cy, cz).  A float32
+// pre-test on the cell-relative offsets (candidate offset + its cell delta *
+// s against the target's offset) drops the candidates that are certainly
+// outside the support: its threshold 4h^2 (1 + 1e-5) lies above the float32
+// error of the offsets (about 1e-6 of 4h^2) and the float64 test that follows
+// decides every pair exactly as before, so the pairs and every float64 result
+// are those of the float64 test alone; the float64 unit, the scarce resource
+// here, evaluates only the candidates near the support.
 template <bool MOMENTUM>
 __device__ __forceinline__ void runs64(const DevParams &P, int self, const double4_32a &pa,
-                                       const double4_32a &va, double ca, int cx, int cy, int cz,
-                                       const double4_32a *__restrict__ posp,
+                                       const float4 &fa, const double4_32a &va, double ca, int cx,
+                                       int cy, int cz, const double4_32a *__restrict__ posp,
+                                       const float4 *__restrict__ posf,
                                        const double4_32a *__restrict__ velr,
                                        const int32_t *__restrict__ start, Acc64 &o)
 {
     const double s2 = 4.0 * P.h * P.h;
+    const float s2f = P.four_h2f * (1.0f + 1e-5f);
     const int R = P.reach;
     int x0 = max(cx - R, 0), x1 = min(cx + R, P.nx - 1);
     for (int dz = -R; dz <= R; ++dz) {
         int z = cz + dz;
         if (z < 0 || z >= P.nz) continue;
+        const float za = fa.z - (float)dz * P.sf;
         for (int dy = -R; dy <= R; ++dy) {
             int y = cy + dy;
             if (y < 0 || y >= P.ny) continue;
+            const float ya = fa.y - (float)dy * P.sf;
             int row = P.nx * (y + P.ny * z);
             int j0 = start[row + x0], j1 = start[row + x1 + 1];
+            // first index of cells x-R+1 .. x+R: a candidate lies in cell
+            // x - R + (number of these at or below its index)
+            int cut[4];
+            for (int u = 0; u < 2 * R; ++u) cut[u] = start[row + min(max(cx - R + 1 + u, 0), P.nx)];
             for (int j = j0; j < j1; ++j) {
                 if (j == self) continue;
+                int k = -R;
+                for (int u = 0; u < 2 * R; ++u) k += j >= cut[u] ? 1 : 0;
+                const float4 fb = posf[j];
+                const float ex = fa.x - (float)k * P.sf - fb.x, ey = ya - fb.y, ez = za - fb.z;
+                if (!(fmaf(ex, ex, fmaf(ey, ey, ez * ez)) < s2f)) continue;
                 double4_32a pb = posp[j];
                 double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
                 double r2 = rx * rx + ry * ry + rz * rz;
@@ -128,6 +149,7 @@ k_pi_fluid64(int nf, DevParams P, const double4_32a *__restrict__ posp,
              const double4_32a *__restrict__ velr, const uint32_t *__restrict__ cell,
              const int32_t *__restrict__ fstart, const double4_32a *__restrict__ bposp,
              const double4_32a *__restrict__ bvelr, const int32_t *__restrict__ bstart,
+             const float4 *__restrict__ posf, const float4 *__restrict__ bposf,
              double4_32a *__restrict__ acc, Scalars *sc)
 {
     __shared__ double red[32];
@@ -136,12 +158,13 @@ k_pi_fluid64(int nf, DevParams P, const double4_32a *__restrict__ posp,
     double f2 = 0.0, vis = 0.0;
     if (i < nvalid) {
         double4_32a pa = posp[i], va = velr[i];
+        const float4 fa = posf[i];
         int cx, cy, cz;
         cell_xyz(P, cell[i], &cx, &cy, &cz);
         double ca = sound64(P, va.w);
         Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
-        runs64<true>(P, i, pa, va, ca, cx, cy, cz, posp, velr, fstart, o);
-        runs64<true>(P, -1, pa, va, ca, cx, cy, cz, bposp, bvelr, bstart, o);
+        runs64<true>(P, i, pa, fa, va, ca, cx, cy, cz, posp, posf, velr, fstart, o);
+        runs64<true>(P, -1, pa, fa, va, ca, cx, cy, cz, bposp, bposf, bvelr, bstart, o);
         double ax = P.mass * o.ax + P.g[0];
         double ay = P.mass * o.ay + P.g[1];
         double az = P.mass * o.az + P.g[2];
@@ -161,6 +184,7 @@ k_pi_boundary64(int nb, DevParams P, const double4_32a *__restrict__ bposp,
                 const double4_32a *__restrict__ bvelr, const uint32_t *__restrict__ bcell,
                 const int32_t *__restrict__ bstart, const double4_32a *__restrict__ posp,
                 const double4_32a *__restrict__ velr, const int32_t *__restrict__ fstart,
+                const float4 *__restrict__ bposf, const float4 *__restrict__ posf,
                 double *__restrict__ bar, Scalars *sc)
 {
     __shared__ double red[32];
@@ -169,10 +193,11 @@ k_pi_boundary64(int nb, DevParams P, const double4_32a *__restrict__ bposp,
     double vis = 0.0;
     if (i < nvalid) {
         double4_32a pa = bposp[i], va = bvelr[i];
+        const float4 fa = bposf[i];
         int cx, cy, cz;
         cell_xyz(P, bcell[i], &cx, &cy, &cz);
         Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
-        runs64<false>(P, -1, pa, va, 0.0, cx, cy, cz, posp, velr, fstart, o);
+        runs64<false>(P, -1, pa, fa, va, 0.0, cx, cy, cz, posp, posf, velr, fstart, o);
         bar[i] = P.mass * o.ar;
         vis = o.vis;
     } else if (i < nb) {
@@ -262,12 +287,12 @@ int pi_launch(sph_ctx *ctx)
             SPH_LAUNCH(ctx, k_pi_fluid64, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
                        (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
-                       (double4_32a *)w.acc, w.sc);
+                       w.posf, w.bposf, (double4_32a *)w.acc, w.sc);
         if (nb > 0)
             SPH_LAUNCH(ctx, k_pi_boundary64, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
-                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, (double *)w.bar,
-                       w.sc);
+                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, w.bposf,
+                       w.posf, (double *)w.bar, w.sc);
     }
     return check_cuda(cudaGetLastError());
 }

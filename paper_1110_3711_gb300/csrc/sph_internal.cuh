@@ -76,6 +76,7 @@ struct Workspace {
     size_t state_chunk_bytes;
     // packed PI inputs / outputs (fluid)
     void *posp, *velr, *acc;
+    float4 *posf, *bposf;     // SPH_FP64: float32 offsets from the cell origin (pre-test of PI)
     uint32_t *cell;
     // boundary
     double *bx, *by, *bz;
