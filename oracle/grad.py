@@ -9,7 +9,9 @@ formulation; see that file for the references).
 
 State (persistent-id order, fluid first): x [N,3], v [N,3] (boundary rows 0),
 u = v^{n-1}, rho [N], sig = rho^{n-1}.  Objective: the mean over sensors and
-over the recorded states of the Shepard-interpolated pressure.
+over the recorded states of the Shepard-interpolated pressure, or (front_tau
+given) the mean over the recorded states of the front position, the smooth
+maximum tau log sum_a exp(x_a / tau) of the fluid x coordinates.
 """
 from __future__ import annotations
 
@@ -115,10 +117,16 @@ def sensor_pressure(p, nf, x, rho, spos):
                        torch.zeros_like(den))
 
 
-def objective(case, vel0, alpha, steps, dt, window, spos):
+def front_position(nf, x, tau):
+    """Front of the fluid: the smooth maximum tau log sum_a exp(x_a / tau) of the
+    fluid x coordinates (it lies between max x and max x + tau log nf)."""
+    return tau * torch.logsumexp(x[:nf, 0] / tau, 0)
+
+
+def objective(case, vel0, alpha, steps, dt, window, spos, front_tau=None):
     """J = mean over sensors and over the states after steps (steps-window, steps]
-    of the sensor pressure.  vel0: fluid initial velocity [nf,3] tensor;
-    alpha: 0-d tensor."""
+    of the sensor pressure, or of the front position when front_tau is given.
+    vel0: fluid initial velocity [nf,3] tensor; alpha: 0-d tensor."""
     p = case.params
     nf = case.n_f
     x = torch.as_tensor(case.pos, dtype=DT)
@@ -131,20 +139,23 @@ def objective(case, vel0, alpha, steps, dt, window, spos):
     for n in range(steps):
         x, v, u, rho, sig = step(p, nf, x, v, u, rho, sig, alpha, n, dt)
         if n + 1 > steps - window:
-            acc = acc + sensor_pressure(p, nf, x, rho, spos).sum()
-    return acc / (len(spos) * window)
+            if front_tau is None:
+                acc = acc + sensor_pressure(p, nf, x, rho, spos).sum()
+            else:
+                acc = acc + front_position(nf, x, front_tau)
+    return acc / ((len(spos) if front_tau is None else 1) * window)
 
 
-def gradient(case, vel0, alpha, steps, dt, window, spos):
+def gradient(case, vel0, alpha, steps, dt, window, spos, front_tau=None):
     """(J, dJ/dvel0 [nf,3], dJ/dalpha) by autograd."""
     v0 = torch.as_tensor(vel0, dtype=DT).clone().requires_grad_(True)
     a = torch.tensor(float(alpha), dtype=DT, requires_grad=True)
-    J = objective(case, v0, a, steps, dt, window, spos)
+    J = objective(case, v0, a, steps, dt, window, spos, front_tau)
     gv, ga = torch.autograd.grad(J, (v0, a))
     return float(J.detach()), gv.numpy(), float(ga)
 
 
-def objective_c(case, vel0, alpha, steps, dt, window, spos):
+def objective_c(case, vel0, alpha, steps, dt, window, spos, front_tau=None):
     """The same objective evaluated by the C oracle (for finite differences)."""
     import copy
     p = copy.copy(case.params)
@@ -157,5 +168,10 @@ def objective_c(case, vel0, alpha, steps, dt, window, spos):
     for n in range(steps):
         st.step()
         if n + 1 > steps - window:
-            acc += O.sensor_pressure(p, case.n_f, st.pos, st.rho, spos).sum()
-    return acc / (len(spos) * window)
+            if front_tau is None:
+                acc += O.sensor_pressure(p, case.n_f, st.pos, st.rho, spos).sum()
+            else:
+                xs = st.pos[:case.n_f, 0] / front_tau
+                m = xs.max()
+                acc += front_tau * (m + math.log(np.exp(xs - m).sum()))
+    return acc / ((len(spos) if front_tau is None else 1) * window)

@@ -6,6 +6,7 @@ smooth case (no viscosity switch, no boundary clamp) and to the FD noise of
 the C0 viscosity switch on the dam break.
 """
 import copy
+import math
 
 import numpy as np
 import pytest
@@ -84,3 +85,42 @@ def test_gradient_dam_break_matches_finite_differences(oracle_lib, G):
     fd_a = (G.objective_c(c, v0, 0.1 + eps, steps, DT, window, spos)
             - G.objective_c(c, v0, 0.1 - eps, steps, DT, window, spos)) / (2 * eps)
     assert fd_a == pytest.approx(ga, rel=1e-6)
+
+
+def test_front_position_closed_forms(oracle_lib, G):
+    """The smooth maximum lies in [max x, max x + tau log n]; n equal values give
+    exactly x + tau log n; for tau far below the spacing it is the maximum."""
+    rng = np.random.default_rng(4)
+    x = torch.as_tensor(rng.uniform(0.0, 0.4, size=(500, 3)))
+    for tau in (1e-3, 1e-2, 0.1):
+        J = float(G.front_position(400, x, tau))
+        m = float(x[:400, 0].max())
+        assert m <= J <= m + tau * math.log(400)
+    same = torch.full((37, 3), 0.25, dtype=torch.float64)
+    assert float(G.front_position(37, same, 0.01)) == pytest.approx(0.25 + 0.01 * math.log(37),
+                                                                    rel=1e-14)
+    assert float(G.front_position(400, x, 1e-6)) == pytest.approx(float(x[:400, 0].max()),
+                                                                  abs=1e-12)
+
+
+def test_front_objective_forward_and_gradient(oracle_lib, G):
+    """Front-position objective (mean over the last states of the smooth maximum
+    of the fluid x, tau = dp): the autograd forward equals the C oracle's, and
+    its gradient matches central differences of the C oracle (eps = 1e-7, the
+    viscosity switch being only C0)."""
+    c = small_dam(0.02)
+    tau = c.params.dp
+    steps, window = 30, 10
+    v0 = c.vel[:c.n_f].copy()
+    J, gv, ga = G.gradient(c, v0, 0.1, steps, DT, window, None, front_tau=tau)
+    Jc = G.objective_c(c, v0, 0.1, steps, DT, window, None, front_tau=tau)
+    assert J == pytest.approx(Jc, rel=1e-12)
+    rng = np.random.default_rng(3)
+    for _ in range(2):
+        d = rng.normal(size=v0.shape)
+        eps = 1e-7
+        jp = G.objective_c(c, v0 + eps * d, 0.1, steps, DT, window, None, front_tau=tau)
+        jm = G.objective_c(c, v0 - eps * d, 0.1, steps, DT, window, None, front_tau=tau)
+        fd = (jp - jm) / (2 * eps)
+        an = float((gv * d).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an)
