@@ -245,6 +245,21 @@ int sph_sensor_pressure(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
 int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n_sensors,
                        const double *dj_dp, double *lam);
 
+/* Front position of the fluid: the smooth maximum J = tau log sum_a exp(x_a / tau)
+ * of the x coordinates of all fluid particles of the current state (between
+ * max x and max x + tau log n_f; tau > 0, e.g. dp), as a differentiable
+ * measure of how far the collapsing column has run.  The paper defines no
+ * objective: this one and the sensor pressures serve the differentiable form.
+ * Output: device double *J.  SPH_ERR_INVALID_ARG without fluid particles or
+ * for tau <= 0.  Asynchronous. */
+int sph_front_position(sph_ctx *ctx, double tau, double *J);
+
+/* Adds to lam (device, layout above) the derivative of dj * J_front with
+ * respect to the current positions: dj exp((x_a - max x) / tau) /
+ * sum_b exp((x_b - max x) / tau) on the x component of fluid particle a.
+ * dj is a host value.  SPH_FP64 only.  Asynchronous. */
+int sph_front_adjoint(sph_ctx *ctx, double tau, double dj, double *lam);
+
 /* Adjoint of one time step at fixed dt (PI + SU, Table 1 formulation; the
  * neighbour relation of the step is a constant of the step).  The context must
  * hold the state at the start of the step (e.g. after sph_load_state of a

@@ -3,11 +3,14 @@
 Forward: the SPH_FP64 time loop at fixed dt, with a checkpoint of the full
 state every ``checkpoint_every`` steps (``sph_save_state`` into torch-owned
 device buffers) and the sensor objective
-    J = mean over the last ``window`` states and over the sensors of P_s.
+    J = mean over the last ``window`` states and over the sensors of P_s,
+or, with ``front_tau`` set, the front objective
+    J = mean over the last ``window`` states of tau log sum_a exp(x_a / tau).
 Backward: for each checkpoint segment in reverse, the segment is recomputed
 from its checkpoint (storing the start state of every step), then the
 hand-written adjoint runs step by step in reverse (``sph_adjoint_step``), adding
-the objective's derivative at every recorded state (``sph_sensor_adjoint``).
+the objective's derivative at every recorded state (``sph_sensor_adjoint`` or
+``sph_front_adjoint``).
 The result is dJ/d(initial fluid velocity) (the initial state has
 v^{-1} = v^0, so both adjoint slots count) and dJ/d(alpha).
 All arithmetic runs in libsph; torch supplies memory and the stream.
@@ -26,17 +29,24 @@ from . import sph as S
 class DamBreakRun:
     """Configuration of one differentiable run (input data, horizon, sensors)."""
 
-    def __init__(self, case, steps, dt, window, sensors, checkpoint_every=20, device="cuda"):
+    def __init__(self, case, steps, dt, window, sensors=None, checkpoint_every=20, device="cuda",
+                 front_tau=None):
         assert 1 <= window <= steps
+        assert (sensors is None) != (front_tau is None), "sensors or front_tau, not both"
         self.case = case
         self.steps = int(steps)
         self.dt = float(dt)
         self.window = int(window)
         self.k = max(1, int(checkpoint_every))
         self.device = torch.device(device)
-        self.sensors = torch.as_tensor(np.ascontiguousarray(sensors, np.float64),
-                                       device=self.device).contiguous()
-        self.n_sensors = int(self.sensors.shape[0])
+        self.front_tau = None if front_tau is None else float(front_tau)
+        if sensors is None:
+            self.sensors = torch.zeros((1, 3), dtype=torch.float64, device=self.device)
+            self.n_sensors = 0
+        else:
+            self.sensors = torch.as_tensor(np.ascontiguousarray(sensors, np.float64),
+                                           device=self.device).contiguous()
+            self.n_sensors = int(self.sensors.shape[0])
         self.sim = None
         self.stats = {}
 
@@ -65,38 +75,51 @@ class DamBreakRun:
         new = lambda: torch.empty(nb, dtype=torch.uint8, device=self.device)
         self.ckpts = [new() for _ in range(nseg)]
         self.final = new()
-        p_buf = torch.zeros(self.n_sensors, dtype=torch.float64, device=self.device)
+        p_buf = torch.zeros(max(self.n_sensors, 1), dtype=torch.float64, device=self.device)
         acc = torch.zeros((), dtype=torch.float64, device=self.device)
         for n in range(self.steps):
             if n % self.k == 0:
                 sim.save_state(self.ckpts[n // self.k])
             sim.neighbour_list()
             if self._recorded(n):
-                S.sph_sensor_pressure(sim.ctx, self.sensors, self.n_sensors, p_buf)
-                acc = acc + p_buf.sum()
+                acc = acc + self._measure(sim, p_buf)
             sim.interact()
             sim.update()
         sim.save_state(self.final)
         sim.neighbour_list()
-        S.sph_sensor_pressure(sim.ctx, self.sensors, self.n_sensors, p_buf)
-        acc = acc + p_buf.sum()
+        acc = acc + self._measure(sim, p_buf)
         self.stats["checkpoint_bytes"] = nb * (nseg + 1)
-        return acc / (self.n_sensors * self.window)
+        return acc / (max(self.n_sensors, 1) * self.window)
+
+    def _measure(self, sim, buf):
+        """The objective's term of the current state (sum over the sensors, or
+        the front position)."""
+        if self.front_tau is None:
+            S.sph_sensor_pressure(sim.ctx, self.sensors, self.n_sensors, buf)
+            return buf.sum()
+        S.sph_front_position(sim.ctx, self.front_tau, buf)
+        return buf[0].clone()
+
+    def _measure_adjoint(self, sim, dj, dj_dp, lam):
+        if self.front_tau is None:
+            S.sph_sensor_adjoint(sim.ctx, self.sensors, self.n_sensors, dj_dp, lam)
+        else:
+            S.sph_front_adjoint(sim.ctx, self.front_tau, dj, lam)
 
     def backward(self, grad_j):
         sim = self.sim
         c = self.case
         N = c.n
         dev = self.device
-        dj_dp = torch.full((self.n_sensors,), float(grad_j) / (self.n_sensors * self.window),
-                           dtype=torch.float64, device=dev)
+        dj = float(grad_j) / (max(self.n_sensors, 1) * self.window)
+        dj_dp = torch.full((max(self.n_sensors, 1),), dj, dtype=torch.float64, device=dev)
         lam = torch.zeros(11 * N, dtype=torch.float64, device=dev)
         lam2 = torch.zeros_like(lam)
         dalpha = torch.zeros(1, dtype=torch.float64, device=dev)
         # the final state
         sim.load_state(self.final)
         sim.neighbour_list()
-        S.sph_sensor_adjoint(sim.ctx, self.sensors, self.n_sensors, dj_dp, lam)
+        self._measure_adjoint(sim, dj, dj_dp, lam)
         nb = sim.checkpoint_bytes()
         snaps = [torch.empty(nb, dtype=torch.uint8, device=dev) for _ in range(self.k)]
         nseg = len(self.ckpts)
@@ -113,7 +136,7 @@ class DamBreakRun:
                 sim.load_state(snaps[n - n0])
                 S.sph_adjoint_step(sim.ctx, lam, lam2, dalpha)
                 if self._recorded(n):
-                    S.sph_sensor_adjoint(sim.ctx, self.sensors, self.n_sensors, dj_dp, lam2)
+                    self._measure_adjoint(sim, dj, dj_dp, lam2)
                 lam, lam2 = lam2, lam
         self.stats["checkpoint_bytes"] += nb * self.k
         nf = c.n_f

@@ -546,6 +546,55 @@ int sensor_launch(sph_ctx *ctx, const double *spos, int S, double *p_out, double
 
 }  // namespace
 
+// Front of the fluid: the smooth maximum J = tau log sum_a exp(x_a / tau) of
+// the fluid x coordinates, computed as m + tau log sum_a exp((x_a - m) / tau)
+// with m = max_a x_a (no overflow).  One block, so every sum is formed in the
+// same order.  Writes front[0] = m, front[1] = the sum and, if J is given, *J.
+__global__ void __launch_bounds__(1024)
+k_front(int nf, double tau, const double *__restrict__ x, double *__restrict__ front,
+        double *__restrict__ J)
+{
+    __shared__ double red[32];
+    __shared__ double sm;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double m = -INFINITY;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) m = fmax(m, x[i]);
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) red[warp] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = red[0];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) t = fmax(t, red[w]);
+        sm = t;
+    }
+    __syncthreads();
+    m = sm;
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) s += exp((x[i] - m) / tau);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    __syncthreads();
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        front[0] = m;
+        front[1] = t;
+        if (J) *J = m + tau * log(t);
+    }
+}
+
+// dJ/dx_a of dj * J_front: dj exp((x_a - m) / tau) / sum, added to the
+// position adjoint of particle a (persistent-id layout).
+__global__ void k_front_adj(int nf, double tau, double dj, const double *__restrict__ x,
+                            const uint32_t *__restrict__ id, const double *__restrict__ front,
+                            double *__restrict__ lam)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nf) return;
+    lam[3 * (size_t)id[i]] += dj * exp((x[i] - front[0]) / tau) / front[1];
+}
+
 }  // namespace sph
 
 using namespace sph;
@@ -621,5 +670,25 @@ extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *la
         SPH_LAUNCH(ctx, k_adj_out, (unsigned)((N + T - 1) / T), T, 0, st, nf, nb, N, w.id[c],
                    w.bid, w.adj_lam, lam);
     if (nf > 0) SPH_LAUNCH(ctx, k_adj_alpha, 1, 1, 0, st, w.adj_part, blocks_f, dalpha);
+    return check_cuda(cudaGetLastError());
+}
+
+extern "C" int sph_front_position(sph_ctx *ctx, double tau, double *J)
+{
+    if (!ctx || !J || !(tau > 0.0) || ctx->nf <= 0) return SPH_ERR_INVALID_ARG;
+    Workspace &w = ctx->w;
+    SPH_LAUNCH(ctx, k_front, 1, 1024, 0, ctx->stream, (int)ctx->nf, tau, w.x[ctx->cur], w.front, J);
+    return check_cuda(cudaGetLastError());
+}
+
+extern "C" int sph_front_adjoint(sph_ctx *ctx, double tau, double dj, double *lam)
+{
+    if (!ctx || !lam || !(tau > 0.0) || ctx->nf <= 0) return SPH_ERR_INVALID_ARG;
+    if (ctx->precision != SPH_FP64) return SPH_ERR_INVALID_ARG;
+    Workspace &w = ctx->w;
+    const int nf = (int)ctx->nf, c = ctx->cur, T = 256;
+    SPH_LAUNCH(ctx, k_front, 1, 1024, 0, ctx->stream, nf, tau, w.x[c], w.front, (double *)nullptr);
+    SPH_LAUNCH(ctx, k_front_adj, (nf + T - 1) / T, T, 0, ctx->stream, nf, tau, dj, w.x[c], w.id[c],
+               w.front, lam);
     return check_cuda(cudaGetLastError());
 }

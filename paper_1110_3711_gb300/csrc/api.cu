@@ -236,6 +236,7 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     }
     W.sens_p = b.take<double>(kMaxSensors);
     W.sens_den = b.take<double>(kMaxSensors);
+    W.front = b.take<double>(2);
     W.stage = b.take<double>((size_t)11 * (size_t)(nf + nb) + 1);
     W.sc = b.take<Scalars>(1);
     W.counts4 = b.take<unsigned long long>(4);

@@ -98,6 +98,7 @@ struct Workspace {
     // in sorted order (11 doubles per particle), per-block dJ/dalpha
     double *adj_gF, *adj_gD, *adj_lam, *adj_part;
     double *sens_p, *sens_den;  // sensor pressures and Shepard denominators
+    double *front;              // front position: max x and the sum of exp((x - max) / tau)
     // host exchange staging: 11 doubles per particle
     double *stage;
     Scalars *sc;

@@ -107,6 +107,8 @@ def lib():
                 "sph_neighbour_list_static": ([pp, i64, vp, vp, vp, vp, vp], i32),
                 "sph_sensor_pressure": ([vp, vp, i64, vp], i32),
                 "sph_sensor_adjoint": ([vp, vp, i64, vp, vp], i32),
+                "sph_front_position": ([vp, C.c_double, vp], i32),
+                "sph_front_adjoint": ([vp, C.c_double, C.c_double, vp], i32),
                 "sph_adjoint_step": ([vp, vp, vp, vp], i32),
                 "sph_error_string": ([i32], C.c_char_p),
                 "sph_destroy": ([vp], None),
@@ -126,7 +128,8 @@ def exported_symbols():
             "sph_status", "sph_get_neighbour_list", "sph_get_grid", "sph_get_forces",
             "sph_count_work", "sph_launch_count", "sph_checkpoint_bytes", "sph_save_state",
             "sph_load_state", "sph_neighbour_list_static", "sph_sensor_pressure",
-            "sph_sensor_adjoint", "sph_adjoint_step", "sph_error_string", "sph_destroy"]
+            "sph_sensor_adjoint", "sph_front_position", "sph_front_adjoint", "sph_adjoint_step",
+            "sph_error_string", "sph_destroy"]
 
 
 def _check(code, what):
@@ -290,6 +293,14 @@ def sph_sensor_pressure(ctx, sensors, n_sensors, out):
 def sph_sensor_adjoint(ctx, sensors, n_sensors, dj_dp, lam):
     _check(lib().sph_sensor_adjoint(ctx, _ptr(sensors), int(n_sensors), _ptr(dj_dp), _ptr(lam)),
            "sph_sensor_adjoint")
+
+
+def sph_front_position(ctx, tau, out):
+    _check(lib().sph_front_position(ctx, float(tau), _ptr(out)), "sph_front_position")
+
+
+def sph_front_adjoint(ctx, tau, dj, lam):
+    _check(lib().sph_front_adjoint(ctx, float(tau), float(dj), _ptr(lam)), "sph_front_adjoint")
 
 
 def sph_adjoint_step(ctx, lam_next, lam, dalpha):

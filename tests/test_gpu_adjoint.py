@@ -86,6 +86,52 @@ def test_adjoint_matches_gpu_finite_differences(torch_mod):
     assert fd_a == pytest.approx(ga, rel=5e-6)
 
 
+def _front_run(torch, case, k, vel0=None, alpha=0.1):
+    from paper_1110_3711_gb300.autograd import DamBreakRun, objective
+    run = DamBreakRun(case, STEPS, DT, WINDOW, None, checkpoint_every=k,
+                      front_tau=case.params.dp)
+    v = case.vel[:case.n_f] if vel0 is None else vel0
+    v0 = torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True)
+    a = torch.tensor(alpha, dtype=torch.float64, device="cuda", requires_grad=True)
+    J = objective(v0, a, run)
+    J.backward()
+    return float(J.detach()), v0.grad.cpu().numpy(), float(a.grad)
+
+
+def test_front_position_value(torch_mod):
+    """sph_front_position is the smooth maximum of the fluid x of the state."""
+    torch = torch_mod
+    from paper_1110_3711_gb300 import sph
+    c = dam_break(0.02)
+    for prec in ("fp64", "fp32"):
+        sim = sph.Simulation.from_case(c, precision=prec)
+        for _ in range(5):
+            sim.step()
+        pos, _, _ = sim.get_state()
+        out = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tau = c.params.dp
+        sph.sph_front_position(sim.ctx, tau, out)
+        xs = pos[:c.n_f, 0] / tau
+        want = tau * (xs.max() + np.log(np.exp(xs - xs.max()).sum()))
+        assert float(out.cpu()) == pytest.approx(want, rel=1e-13)
+
+
+def test_front_objective_matches_oracle_gradient(torch_mod):
+    """Front-position objective (tau = dp) through the adjoint: J and the
+    gradients equal the gradient oracle's; the checkpoint interval changes
+    nothing."""
+    from oracle import grad as G
+    c, _ = _case()
+    Jo, gvo, gao = G.gradient(c, c.vel[:c.n_f], 0.1, STEPS, DT, WINDOW, None,
+                              front_tau=c.params.dp)
+    Jg, gvg, gag = _front_run(torch_mod, c, k=7)
+    assert Jg == pytest.approx(Jo, rel=1e-12)
+    assert np.abs(gvg - gvo).max() <= 1e-8 * np.abs(gvo).max()
+    assert gag == pytest.approx(gao, rel=1e-8, abs=1e-12 * np.abs(gvo).max())
+    J1, gv1, ga1 = _front_run(torch_mod, c, k=STEPS)
+    assert J1 == Jg and np.array_equal(gv1, gvg) and ga1 == gag
+
+
 def test_adjoint_step_needs_fixed_dt_fp64(torch_mod):
     torch = torch_mod
     from paper_1110_3711_gb300 import sph
