@@ -149,24 +149,53 @@ def test_adjoint_step_needs_fixed_dt_fp64(torch_mod):
 def test_adjoint_differentiable_configuration(torch_mod):
     """dp = 0.01 dam break (80,400 fluid + 58,606 boundary), fixed dt = 1e-4 s,
     400 steps, checkpoints every 20 steps, 64 sensors on the wall behind the
-    column, mean over the last 100 states.  Central differences along the
-    normalised gradient (no cancellation between components) and in alpha.
-    The viscosity switch (Pi = 0 for v.r >= 0) is only C0: every pair whose
-    v.r changes sign inside the FD interval adds an O(eps) error, hence the
-    per-check bars."""
+    column, mean over the last 100 states.  Central differences with eps =
+    1e-3 along the normalised gradient (no cancellation between components)
+    agree to 1e-4 (measured 6.8e-6).  In alpha the sensor objective is rougher:
+    the viscosity switch (Pi = 0 for v.r >= 0) is only C0 and a change of alpha
+    moves many pairs across it, each adding an O(eps) error; at eps = 1e-5 the
+    central difference agrees to 1e-3 (measured 3e-4, 2.5e-3 at eps = 1e-3)."""
     torch = torch_mod
-    from paper_1110_3711_gb300.autograd import DamBreakRun
     c = dam_break(0.01, vel_sigma=0.05, seed=0, fixed_dt=1e-4)
     spos = wall_sensors(c, wall="back")
     J, gv, ga, run = _gpu_grad(torch, c, spos, k=20, steps=400, window=100, dt=1e-4)
     assert run.stats["checkpoint_bytes"] < 1e9
     v0 = c.vel[:c.n_f].copy()
     d = gv / np.linalg.norm(gv)
-    eps = 1e-4
+    eps = 1e-3
     fd = (_gpu_j(torch, c, spos, v0 + eps * d, 0.1, steps=400, window=100, dt=1e-4)
           - _gpu_j(torch, c, spos, v0 - eps * d, 0.1, steps=400, window=100, dt=1e-4)) / (2 * eps)
-    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-3)
+    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-4)
     eps = 1e-5
     fd_a = (_gpu_j(torch, c, spos, v0, 0.1 + eps, steps=400, window=100, dt=1e-4)
             - _gpu_j(torch, c, spos, v0, 0.1 - eps, steps=400, window=100, dt=1e-4)) / (2 * eps)
     assert fd_a == pytest.approx(ga, rel=1e-3)
+
+
+@pytest.mark.slow
+def test_front_objective_differentiable_configuration(torch_mod):
+    """The same configuration with the front-position objective (tau = dp, mean
+    over the last 100 states): central differences with eps = 1e-3 along the
+    normalised velocity gradient and in alpha agree to 1e-4 (measured 7e-7 and
+    2.3e-6)."""
+    torch = torch_mod
+    from paper_1110_3711_gb300.autograd import DamBreakRun, objective
+    c = dam_break(0.01, vel_sigma=0.05, seed=0, fixed_dt=1e-4)
+    tau = c.params.dp
+
+    def run_j(v, al):
+        r = DamBreakRun(c, 400, 1e-4, 100, checkpoint_every=400, front_tau=tau)
+        return float(r.forward(torch.tensor(v, dtype=torch.float64, device="cuda"), al))
+
+    run = DamBreakRun(c, 400, 1e-4, 100, checkpoint_every=20, front_tau=tau)
+    v0t = torch.tensor(c.vel[:c.n_f], dtype=torch.float64, device="cuda", requires_grad=True)
+    a = torch.tensor(0.1, dtype=torch.float64, device="cuda", requires_grad=True)
+    objective(v0t, a, run).backward()
+    gv, ga = v0t.grad.cpu().numpy(), float(a.grad)
+    v0 = c.vel[:c.n_f].copy()
+    d = gv / np.linalg.norm(gv)
+    eps = 1e-3
+    fd = (run_j(v0 + eps * d, 0.1) - run_j(v0 - eps * d, 0.1)) / (2 * eps)
+    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-4)
+    fd_a = (run_j(v0, 0.1 + eps) - run_j(v0, 0.1 - eps)) / (2 * eps)
+    assert fd_a == pytest.approx(ga, rel=1e-4)
