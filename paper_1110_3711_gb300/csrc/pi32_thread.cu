@@ -9,7 +9,7 @@
 //                  k_cell_ranges and read by the kernel (Fig. 11 bottom)
 // Kept as selectable variants of sph_interact so that the paper's GPU
 // optimisations can be measured on GB300 beside the warp-cooperative kernel
-// (pi_kernel = 0, pi32.cu); the arithmetic of a pair is the same.
+// (pi_kernel = 0, pi32.cu); the arithmetic of a pair is the same (pair_t).
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -24,24 +24,46 @@ struct AccT {
     float ax, ay, az, ar, vis;
 };
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float x)
+{
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// Pair terms with the arithmetic of the warp kernel (pi32.cu), in units of h:
+// r' = r / h, q = |r'|, F'' = (kA h / kB)(2.25 q - 3) for q < 1 and
+// (2 - q)^2 / q otherwise, mu = v.r' / (q^2 + eta^2/h^2), -alpha c_b =
+// (-alpha c0 / rho0^3) rho_b^3; the sums hold (P_a/rho_a^2 + P_b/rho_b^2 + Pi)
+// F'' r' and (v.r') F'', and the factors -m kB and m kB are applied once per
+// target.  cpa = -alpha c_a; r_ab comes in metres.
 template <bool MOMENTUM>
 __device__ __forceinline__ void pair_t(const DevParams &P, const float4 &pa, const float4 &va,
-                                       float ca, const float4 &pb, const float4 &vb, float rx,
-                                       float ry, float rz, float r2, AccT &o)
+                                       float cpa, const float4 &pb, const float4 &vb, float rx,
+                                       float ry, float rz, AccT &o)
 {
-    float rinv = rsqrtf(fmaxf(r2, 1e-30f));
-    float r = r2 * rinv;
-    float q = r * P.invhf;
-    float t = 2.0f - q;
-    float F = q < 1.0f ? P.kA * fmaf(2.25f, q, -3.0f) : P.kB * t * t * rinv;
-    float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
-    float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
-    float mu = __fdividef(P.hf * vdr, r2 + P.eta2f);
+    rx *= P.invhf;
+    ry *= P.invhf;
+    rz *= P.invhf;
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
+    const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+    const float q = r2 * rinv;
+    const float t = 2.0f - q;
+    const float F = q < 1.0f ? fmaf(P.gw1, q, P.gw0) : t * t * rinv;
+    const float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
+    const float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
+    const float mu = vdr * rcp_approx(r2 + P.eta2_h2f);
     if (MOMENTUM) {
-        float rb = vb.w * P.inv_rho0f;
-        float cb = P.c0f * rb * rb * rb;
-        float Pi = vdr < 0.0f ? -P.alphaf * __fdividef((ca + cb) * mu, va.w + vb.w) : 0.0f;
-        float coef = -(pa.w + pb.w + Pi) * F;
+        const float cc = fmaf(P.kcf, vb.w * vb.w * vb.w, cpa);
+        const float coef =
+            fmaf(cc * fminf(mu, 0.0f), rcp_approx(va.w + vb.w), pa.w + pb.w) * F;
         o.ax = fmaf(coef, rx, o.ax);
         o.ay = fmaf(coef, ry, o.ay);
         o.az = fmaf(coef, rz, o.az);
@@ -69,7 +91,7 @@ __device__ __forceinline__ void walk_range(const DevParams &P, const float4 &pa,
         float4 pb = posp[j];
         float rx = xa - pb.x, ry = ya - pb.y, rz = za - pb.z;
         float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-        if (r2 < P.four_h2f) pair_t<MOMENTUM>(P, pa, va, ca, pb, velr[j], rx, ry, rz, r2, o);
+        if (r2 < P.four_h2f) pair_t<MOMENTUM>(P, pa, va, ca, pb, velr[j], rx, ry, rz, o);
     }
 }
 
@@ -130,14 +152,14 @@ k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
         const int cx = (int)(c - t * (uint32_t)P.nx), cy = (int)(t % (uint32_t)P.ny),
                   cz = (int)(t / (uint32_t)P.ny);
         const float ra = va.w * P.inv_rho0f;
-        const float ca = P.c0f * ra * ra * ra;
+        const float ca = P.nalphaf * (P.c0f * ra * ra * ra);  // -alpha c_a
         AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, posp, velr, fstart, franges, o);
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, bposp, bvelr, bstart, branges, o);
-        const float ax = fmaf(P.massf, o.ax, P.gf[0]);
-        const float ay = fmaf(P.massf, o.ay, P.gf[1]);
-        const float az = fmaf(P.massf, o.az, P.gf[2]);
-        acc[i] = make_float4(ax, ay, az, P.massf * o.ar);
+        const float ax = fmaf(P.nmkBf, o.ax, P.gf[0]);
+        const float ay = fmaf(P.nmkBf, o.ay, P.gf[1]);
+        const float az = fmaf(P.nmkBf, o.az, P.gf[2]);
+        acc[i] = make_float4(ax, ay, az, P.mkBf * o.ar);
         f2 = (double)ax * ax + (double)ay * ay + (double)az * az;
         vis = (double)o.vis;
         if (!(f2 < INFINITY) || !(o.ar == o.ar)) atomicOr(&sc->flags, SPH_FLAG_NAN);
@@ -166,7 +188,7 @@ k_pi_thread_boundary(int nb, DevParams P, const float4 *__restrict__ bposp,
                   cz = (int)(t / (uint32_t)P.ny);
         AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
         runs_t<false, FAST, R>(P, pa, va, 0.f, c, cx, cy, cz, posp, velr, fstart, franges, o);
-        bar[i] = P.massf * o.ar;
+        bar[i] = P.mkBf * o.ar;
         vis = (double)o.vis;
     }
     block_max_to(&sc->mx.visc, vis, red);
