@@ -22,7 +22,12 @@
 //      gradient, Tait pressure, artificial viscosity, continuity) from the
 //      staged data, recomputing r_ab exactly from the shifted offsets.
 // Work items are taken from a list built by NL with an atomic counter, so the
-// grid is persistent (one resident set of CTAs) and balances itself.  Sums of
+// grid is persistent (one resident set of CTAs) and balances itself.  Boundary
+// targets (B-F) come in packed items: consecutive cells of one x row with at
+// most 32 particles together (a boundary cell holds about 10), the candidates
+// being the fluid of the union of their neighbourhoods (x-runs from the first
+// cell - 1 to the last + 1); each candidate is shifted by its own cell's x
+// distance from the first cell, each target by its cell's.  Sums of
 // a target are accumulated by one lane in candidate order, so results do not
 // depend on the order the items are processed in.
 #include <cuda_runtime.h>
@@ -149,7 +154,7 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
        const float4 *__restrict__ fvelr, const int32_t *__restrict__ fstart,
        const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
        const int32_t *__restrict__ bstart, float4 *__restrict__ acc, float *__restrict__ bar,
-       Scalars *sc)
+       const uint32_t *__restrict__ fcell, Scalars *sc)
 {
     __shared__ WarpSmem smem[WARPS];
     __shared__ double red[32];
@@ -167,10 +172,17 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
 
-        // ---- the item: targets [i0, i0 + nt) of cell c
-        const int i0 = (int)items[it];
+        // ---- the item: fluid targets [i0, i0 + nt) of cell c; boundary
+        // targets [i0, i0 + nt) of cells c .. c + (cx1 - cx) of one x row
+        int i0, nt;
+        if (MOMENTUM) {
+            i0 = (int)items[it];
+            nt = min(32, tstart[tcell[i0] + 1] - i0);
+        } else {
+            i0 = (int)items[2 * it];
+            nt = (int)items[2 * it + 1];
+        }
         const uint32_t c = tcell[i0];
-        const int nt = min(32, tstart[c + 1] - i0);
         const bool active = lane < nt;
         const int i = i0 + (active ? lane : 0);
         const float4 pa = tposp[i], va = tvelr[i];
@@ -178,7 +190,10 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
         const int cx = (int)(c - cyz * (uint32_t)P.nx);
         const int cy = (int)(cyz % (uint32_t)P.ny);
         const int cz = (int)(cyz / (uint32_t)P.ny);
-        const float xa = pa.x * P.invhf, ya = pa.y * P.invhf, za = pa.z * P.invhf;
+        // last cell of the item (same row) and the target's own x distance
+        const int cx1 = MOMENTUM ? cx : cx + (int)(tcell[i0 + nt - 1] - c);
+        const float tshift = MOMENTUM ? 0.0f : (float)(int)(tcell[i] - c) * P.s_hf;
+        const float xa = fmaf(pa.x, P.invhf, tshift), ya = pa.y * P.invhf, za = pa.z * P.invhf;
         const float m2x = -2.0f * xa, m2y = -2.0f * ya, m2z = -2.0f * za;
         const float thr = active ? 4.0f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
         const float ra = va.w * P.inv_rho0f;
@@ -197,11 +212,15 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                 if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
                     const int32_t *st = list ? bstart : fstart;
                     const int row = P.nx * (y + P.ny * z);
-                    const int x0 = max(cx - 1, 0), x1 = min(cx + 1, P.nx - 1);
+                    const int x0 = max(cx - 1, 0), x1 = min(cx1 + 1, P.nx - 1);
                     j0 = st[row + x0];
                     L = st[row + x1 + 1] - j0;
-                    b1 = st[row + cx];
-                    b2 = st[row + cx + 1];
+                    if (MOMENTUM) {
+                        b1 = st[row + cx];
+                        b2 = st[row + cx + 1];
+                    } else {
+                        b1 = row + cx;  // cell id of the item's first cell in this row
+                    }
                 }
             }
             int pe = L;
@@ -239,7 +258,8 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
                     const int prev = r ? S.run[r - 1].x : 0;
                     const int j = ri.y + (s - prev);
                     const int cd = S.code[r];
-                    const float sx = j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf);
+                    const float sx = MOMENTUM ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
+                                              : (float)((int)fcell[j] - ri.z) * P.s_hf;
                     const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
                     const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
                     float4 p;
@@ -322,25 +342,46 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
     block_max_to(&sc->mx.visc, (double)vismax, red);
 }
 
-// Work items of the boundary list (built once): every 32nd particle of a cell.
-__global__ void k_boundary_items(int nb, DevParams P, const uint32_t *__restrict__ bcell,
-                                 const int32_t *__restrict__ bstart, uint32_t *__restrict__ items,
-                                 uint32_t *__restrict__ count)
+// Work items of the boundary list (built once per list), one thread: runs of
+// consecutive cells of one x row are packed into an item while their particles
+// number 32 at most; a cell of more than 32 particles gives items of 32.  Each
+// item is {first particle, number of particles}; *count is the number of items.
+__global__ void k_pack_boundary_items(DevParams P, const uint32_t *__restrict__ bcell,
+                                      const int32_t *__restrict__ bstart,
+                                      uint32_t *__restrict__ items, uint32_t *__restrict__ count)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
-    bool item = false;
-    if (i < nb && i < bstart[P.ncells]) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int n = bstart[P.ncells];  // particles inside the grid
+    uint32_t k = 0;
+    int i = 0;
+    while (i < n) {
         uint32_t c = bcell[i];
-        item = ((i - bstart[c]) & 31) == 0;
+        int m = bstart[c + 1] - i;
+        if (m > 32) {
+            for (int o = 0; o < m; o += 32) {
+                items[2 * k] = (uint32_t)(i + o);
+                items[2 * k + 1] = (uint32_t)min(32, m - o);
+                ++k;
+            }
+            i += m;
+            continue;
+        }
+        const int first = i;
+        int nt = m;
+        i += m;
+        while (i < n) {
+            const uint32_t c2 = bcell[i];
+            const int m2 = bstart[c2 + 1] - i;
+            if (c2 != c + 1 || (c2 % (uint32_t)P.nx) == 0u || nt + m2 > 32) break;
+            nt += m2;
+            c = c2;
+            i += m2;
+        }
+        items[2 * k] = (uint32_t)first;
+        items[2 * k + 1] = (uint32_t)nt;
+        ++k;
     }
-    unsigned ball = __ballot_sync(0xffffffffu, item);
-    if (ball) {
-        int lane = threadIdx.x & 31;
-        uint32_t base = 0;
-        if (lane == 0) base = atomicAdd(count, (uint32_t)__popc(ball));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
-    }
+    *count = k;
 }
 
 }  // namespace
@@ -373,8 +414,9 @@ int boundary_items_launch(sph_ctx *ctx)
     if (nb == 0) return SPH_OK;
     Workspace &w = ctx->w;
     const int T = 256;
-    SPH_LAUNCH(ctx, k_boundary_items, (nb + T - 1) / T, T, 0, ctx->stream, nb, ctx->dp, w.bcell,
-               w.bstart, w.items_b, &w.ctr[3]);
+    (void)T;
+    SPH_LAUNCH(ctx, k_pack_boundary_items, 1, 32, 0, ctx->stream, ctx->dp, w.bcell, w.bstart,
+               w.items_b, &w.ctr[3]);
     return check_cuda(cudaGetLastError());
 }
 
@@ -390,20 +432,22 @@ int pi32_launch(sph_ctx *ctx)
                        w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
                        (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
                        (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
-                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr, w.sc);
+                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr,
+                       w.cell, w.sc);
         else
             SPH_LAUNCH(ctx, (k_pi32<true, false>), ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp,
                        w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
                        (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
                        (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
-                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr, w.sc);
+                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr,
+                       w.cell, w.sc);
     }
     if (ctx->nb > 0)
         SPH_LAUNCH(ctx, (k_pi32<false, false>), ctx->pi_grid_b, WARPS * 32, 0, st, ctx->dp, w.items_b,
                    &w.ctr[3], &w.ctr[2], (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell,
                    w.bstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
                    (const float4 *)nullptr, (const float4 *)nullptr, w.bstart, (float4 *)nullptr,
-                   (float *)w.bar, w.sc);
+                   (float *)w.bar, w.cell, w.sc);
     return check_cuda(cudaGetLastError());
 }
 

@@ -88,7 +88,8 @@ struct Workspace {
     uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
     uint32_t *count;          // [ncells + 2], then the work-item counters ctr
     uint32_t *ctr;            // [0] fluid items, [1] fluid next, [2] boundary next, [3] boundary items
-    uint32_t *items_f, *items_b;  // PI work items: first target index of a (cell, 32-target chunk)
+    uint32_t *items_f, *items_b;  // PI work items: fluid, first target of a (cell, 32-target chunk);
+                                  // boundary, {first, count} of packed cells of one x row
     int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
     int32_t *fstart, *bstart; // [ncells + 2]
     double *origin;           // cell origins min_d + c s along x (nx), y (ny), z (nz)
