@@ -46,34 +46,73 @@ __device__ __forceinline__ double sound_of(const DevParams &P, double rho)
     return P.gamma_is_7 ? P.c0 * r * r * r : P.c0 * pow(r, 0.5 * (P.gamma - 1.0));
 }
 
+// Terms of one particle that the pair derivatives use, formed once per
+// particle: rho, 1/rho, P/rho^2, the sound speed c, d(P/rho^2)/drho =
+// (c^2 - 2 rho P/rho^2) / rho^2 and dc/drho = c (gamma - 1) / (2 rho).
+struct PartTerms {
+    double rho, ir, pr, c, dpr, dc;
+};
+
+__device__ __forceinline__ PartTerms part_terms(const DevParams &P, double rho, double pr)
+{
+    PartTerms t;
+    t.rho = rho;
+    t.ir = 1.0 / rho;
+    t.pr = pr;
+    t.c = sound_of(P, rho);
+    t.dpr = t.ir * t.ir * (t.c * t.c - 2.0 * pr * rho);
+    t.dc = 0.5 * (P.gamma - 1.0) * t.c * t.ir;
+    return t;
+}
+
+// Terms of a pair that do not change when a and b swap (r -> -r, v -> -v):
+// the kernel factor F(r) (grad_a W = F r), (dF/dr) / r, v.r, 1/(r^2 + eta^2),
+// mu = h v.r / (r^2 + eta^2) and 1/(rho_a + rho_b).  One reciprocal square
+// root and two reciprocals; every other quotient below is a product.
+struct PairGeo {
+    double F, dFr, vdr, iden, mu, iS;
+};
+
+__device__ __forceinline__ PairGeo pair_geo(const DevParams &P, double rx, double ry, double rz,
+                                            double vx, double vy, double vz, double rho_a,
+                                            double rho_b)
+{
+    PairGeo g;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    const double irl = rsqrt(r2);
+    const double q = r2 * irl * P.invh;
+    double dF;
+    if (q < 1.0) {
+        g.F = P.kA64 * (-3.0 + 2.25 * q);
+        dF = P.kA64 * 2.25 * P.invh;
+    } else {
+        const double t = 2.0 - q;
+        g.F = P.kB64 * t * t * irl;
+        dF = P.kB64 * (-2.0 * t * P.invh * irl - t * t * irl * irl);
+    }
+    g.dFr = dF * irl;
+    g.vdr = vx * rx + vy * ry + vz * rz;
+    g.iden = 1.0 / (r2 + P.eta2);
+    g.mu = P.h * g.vdr * g.iden;
+    g.iS = 1.0 / (rho_a + rho_b);
+    return g;
+}
+
 // Derivatives of L = gF . f_ab + gD d_ab for the ordered pair a <- b.
 //   f_ab = -m (P_a/rho_a^2 + P_b/rho_b^2 + Pi) F r     (when momentum)
 //   d_ab = m (v_ab . r) F,   grad_a W = F r
-__device__ __forceinline__ void pair_vjp(const DevParams &P, bool momentum, double rx, double ry,
-                                         double rz, double vx, double vy, double vz, double rho_a,
-                                         double rho_b, double P_a, double P_b, double c_a,
-                                         double c_b, double gFx, double gFy, double gFz,
-                                         double gD, PairGrad &g)
+// r and v are r_ab and v_ab of this direction; G holds the direction-free terms.
+__device__ __forceinline__ void pair_vjp(const DevParams &P, bool momentum, const PairGeo &G,
+                                         double rx, double ry, double rz, double vx, double vy,
+                                         double vz, const PartTerms &A, const PartTerms &B,
+                                         double gFx, double gFy, double gFz, double gD,
+                                         PairGrad &g)
 {
     const double m = P.mass;
-    double r2 = rx * rx + ry * ry + rz * rz;
-    double rl = sqrt(r2);
-    double q = rl * P.invh;
-    double F, dF;  // F(r) and dF/dr
-    if (q < 1.0) {
-        F = P.kA64 * (-3.0 + 2.25 * q);
-        dF = P.kA64 * 2.25 * P.invh;
-    } else {
-        double t = 2.0 - q;
-        F = P.kB64 * t * t / rl;
-        dF = P.kB64 * (-2.0 * t * P.invh / rl - t * t / r2);
-    }
-    double gx = dF * rx / rl, gy = dF * ry / rl, gz = dF * rz / rl;  // grad_r F
-    double vdr = vx * rx + vy * ry + vz * rz;
-    double den = r2 + P.eta2;
-    double mu = P.h * vdr / den;
+    const double F = G.F, vdr = G.vdr, mu = G.mu;
+    const double gx = G.dFr * rx, gy = G.dFr * ry, gz = G.dFr * rz;  // grad_r F
     // continuity
-    double cg = gD * m;
+    const double cg = gD * m;
     g.rx = cg * (F * vx + vdr * gx);
     g.ry = cg * (F * vy + vdr * gy);
     g.rz = cg * (F * vz + vdr * gz);
@@ -84,41 +123,35 @@ __device__ __forceinline__ void pair_vjp(const DevParams &P, bool momentum, doub
     g.rho_b = 0.0;
     g.alpha = 0.0;
     if (!momentum) return;
-    double sF = gFx * rx + gFy * ry + gFz * rz;
-    double S = rho_a + rho_b;
+    const double sF = gFx * rx + gFy * ry + gFz * rz;
+    const double cs = A.c + B.c;
     double K = 0.0, Pi = 0.0;
     if (vdr < 0.0) {
-        K = -P.alpha * (c_a + c_b) / S;
+        K = -P.alpha * cs * G.iS;
         Pi = K * mu;
     }
-    double pr_a = P_a / (rho_a * rho_a), pr_b = P_b / (rho_b * rho_b);
-    double Q = pr_a + pr_b + Pi;
+    const double Q = A.pr + B.pr + Pi;
     // L_m = -m Q F sF
-    double A = -m * Q * sF;   // times grad_r F
-    double Bc = -m * Q * F;   // times gF
-    double Cc = -m * F * sF;  // times dQ
+    const double Aq = -m * Q * sF;   // times grad_r F
+    const double Bc = -m * Q * F;    // times gF
+    const double Cc = -m * F * sF;   // times dQ
     // dPi/dr = K (h v / den - 2 h vdr r / den^2),  dPi/dv = K h r / den
-    double kv = K * P.h / den, kr = -2.0 * K * P.h * vdr / (den * den);
-    g.rx += A * gx + Bc * gFx + Cc * (kv * vx + kr * rx);
-    g.ry += A * gy + Bc * gFy + Cc * (kv * vy + kr * ry);
-    g.rz += A * gz + Bc * gFz + Cc * (kv * vz + kr * rz);
+    const double kv = K * P.h * G.iden, kr = -2.0 * K * P.h * vdr * G.iden * G.iden;
+    g.rx += Aq * gx + Bc * gFx + Cc * (kv * vx + kr * rx);
+    g.ry += Aq * gy + Bc * gFy + Cc * (kv * vy + kr * ry);
+    g.rz += Aq * gz + Bc * gFz + Cc * (kv * vz + kr * rz);
     g.vx += Cc * kv * rx;
     g.vy += Cc * kv * ry;
     g.vz += Cc * kv * rz;
-    // d(P/rho^2)/drho = c^2/rho^2 - 2 P/rho^3;  dc/drho = c (gamma - 1) / (2 rho)
-    double dpr_a = c_a * c_a / (rho_a * rho_a) - 2.0 * P_a / (rho_a * rho_a * rho_a);
-    double dpr_b = c_b * c_b / (rho_b * rho_b) - 2.0 * P_b / (rho_b * rho_b * rho_b);
     double dPi_a = 0.0, dPi_b = 0.0;
     if (vdr < 0.0) {
-        double dca = c_a * (P.gamma - 1.0) / (2.0 * rho_a);
-        double dcb = c_b * (P.gamma - 1.0) / (2.0 * rho_b);
-        double cs = c_a + c_b;
-        dPi_a = -P.alpha * mu * (dca / S - cs / (S * S));
-        dPi_b = -P.alpha * mu * (dcb / S - cs / (S * S));
-        g.alpha = Cc * (-cs * mu / S);
+        const double iS2 = G.iS * G.iS;
+        dPi_a = -P.alpha * mu * (A.dc * G.iS - cs * iS2);
+        dPi_b = -P.alpha * mu * (B.dc * G.iS - cs * iS2);
+        g.alpha = Cc * (-cs * mu * G.iS);
     }
-    g.rho_a = Cc * (dpr_a + dPi_a);
-    g.rho_b = Cc * (dpr_b + dPi_b);
+    g.rho_a = Cc * (A.dpr + dPi_a);
+    g.rho_b = Cc * (B.dpr + dPi_b);
 }
 
 __device__ __forceinline__ void cell_coords(const DevParams &P, uint32_t c, int *cx, int *cy,
@@ -280,7 +313,7 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
     double dal = 0.0;
     if (i < fstart[P.ncells]) {
         const double4_32a pa = posp[i], va = velr[i];
-        const double rho_a = va.w, P_a = pa.w * rho_a * rho_a, c_a = sound_of(P, rho_a);
+        const PartTerms ta = part_terms(P, va.w, pa.w);
         const double gFx = gF[3 * (size_t)i], gFy = gF[3 * (size_t)i + 1],
                      gFz = gF[3 * (size_t)i + 2], gDa = gD[i];
         double lx = 0, ly = 0, lz = 0, lvx = 0, lvy = 0, lvz = 0, lr = 0;
@@ -297,18 +330,18 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
             const double r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < s2)) continue;
             const double4_32a vb = velr[j];
-            const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+            const PartTerms tb = part_terms(P, vb.w, pb.w);
             const double vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
+            const PairGeo G = pair_geo(P, rx, ry, rz, vx, vy, vz, ta.rho, tb.rho);
             // self receives from j
-            pair_vjp(P, true, rx, ry, rz, vx, vy, vz, rho_a, rho_b, P_a, P_b, c_a, c_b, gFx, gFy,
-                     gFz, gDa, g);
+            pair_vjp(P, true, G, rx, ry, rz, vx, vy, vz, ta, tb, gFx, gFy, gFz, gDa, g);
             lx += g.rx; ly += g.ry; lz += g.rz;
             lvx += g.vx; lvy += g.vy; lvz += g.vz;
             lr += g.rho_a;
             dal += g.alpha;
             // j receives from self (r_ji = -r, v_ji = -v)
-            pair_vjp(P, true, -rx, -ry, -rz, -vx, -vy, -vz, rho_b, rho_a, P_b, P_a, c_b, c_a,
-                     gF[3 * (size_t)j], gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gD[j], g);
+            pair_vjp(P, true, G, -rx, -ry, -rz, -vx, -vy, -vz, tb, ta, gF[3 * (size_t)j],
+                     gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gD[j], g);
             lx -= g.rx; ly -= g.ry; lz -= g.rz;
             lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
             lr += g.rho_b;
@@ -320,16 +353,16 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
             const double r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < s2)) continue;
             const double4_32a vb = bvelr[j];
-            const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+            const PartTerms tb = part_terms(P, vb.w, pb.w);
             const double vx = va.x, vy = va.y, vz = va.z;
-            pair_vjp(P, true, rx, ry, rz, vx, vy, vz, rho_a, rho_b, P_a, P_b, c_a, c_b, gFx, gFy,
-                     gFz, gDa, g);
+            const PairGeo G = pair_geo(P, rx, ry, rz, vx, vy, vz, ta.rho, tb.rho);
+            pair_vjp(P, true, G, rx, ry, rz, vx, vy, vz, ta, tb, gFx, gFy, gFz, gDa, g);
             lx += g.rx; ly += g.ry; lz += g.rz;
             lvx += g.vx; lvy += g.vy; lvz += g.vz;
             lr += g.rho_a;
             dal += g.alpha;
-            pair_vjp(P, false, -rx, -ry, -rz, -vx, -vy, -vz, rho_b, rho_a, P_b, P_a, c_b, c_a, 0.0,
-                     0.0, 0.0, gD[(size_t)nf + j], g);
+            pair_vjp(P, false, G, -rx, -ry, -rz, -vx, -vy, -vz, tb, ta, 0.0, 0.0, 0.0,
+                     gD[(size_t)nf + j], g);
             lx -= g.rx; ly -= g.ry; lz -= g.rz;
             lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
         })
@@ -362,7 +395,7 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nb || j >= bstart[P.ncells]) return;
     const double4_32a pb = bposp[j], vb = bvelr[j];
-    const double rho_b = vb.w, P_b = pb.w * rho_b * rho_b, c_b = sound_of(P, rho_b);
+    const PartTerms tb = part_terms(P, vb.w, pb.w);
     const double s2 = 4.0 * P.h * P.h;
     int cx, cy, cz;
     cell_coords(P, bcell[j], &cx, &cy, &cz);
@@ -375,9 +408,10 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
         const double r2 = rx * rx + ry * ry + rz * rz;
         if (!(r2 < s2)) continue;
         const double4_32a va = velr[i];
-        const double rho_a = va.w, P_a = pa.w * rho_a * rho_a, c_a = sound_of(P, rho_a);
-        pair_vjp(P, true, rx, ry, rz, va.x, va.y, va.z, rho_a, rho_b, P_a, P_b, c_a, c_b,
-                 gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2], gD[i], g);
+        const PartTerms ta = part_terms(P, va.w, pa.w);
+        const PairGeo G = pair_geo(P, rx, ry, rz, va.x, va.y, va.z, ta.rho, tb.rho);
+        pair_vjp(P, true, G, rx, ry, rz, va.x, va.y, va.z, ta, tb, gF[3 * (size_t)i],
+                 gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2], gD[i], g);
         lr += g.rho_b;
     })
     lam_s[6 * N + (size_t)nf + j] += lr;
