@@ -34,10 +34,12 @@ namespace {
 
 constexpr int kAdjThreads = 128;
 
-struct PairGrad {
-    double rx, ry, rz;  // dL/dr_ab
-    double vx, vy, vz;  // dL/dv_ab
-    double rho_a, rho_b, alpha;
+// Adjoint sums of one target particle over its pairs.
+struct SelfAdj {
+    double rx, ry, rz;  // lam_x
+    double vx, vy, vz;  // lam_v
+    double rho;         // lam_rho
+    double alpha;       // dJ/dalpha of the pairs the target receives
 };
 
 __device__ __forceinline__ double sound_of(const DevParams &P, double rho)
@@ -46,112 +48,131 @@ __device__ __forceinline__ double sound_of(const DevParams &P, double rho)
     return P.gamma_is_7 ? P.c0 * r * r * r : P.c0 * pow(r, 0.5 * (P.gamma - 1.0));
 }
 
-// Terms of one particle that the pair derivatives use, formed once per
-// particle: rho, 1/rho, P/rho^2, the sound speed c, d(P/rho^2)/drho =
-// (c^2 - 2 rho P/rho^2) / rho^2 and dc/drho = c (gamma - 1) / (2 rho).
+// Terms of one target particle that its pair derivatives use, formed once:
+// rho, P/rho^2, the sound speed c, d(P/rho^2)/drho = (c^2 - 2 rho P/rho^2) / rho^2
+// and dc/drho = c (gamma - 1) / (2 rho).
 struct PartTerms {
-    double rho, ir, pr, c, dpr, dc;
+    double rho, pr, c, dpr, dc;
 };
 
 __device__ __forceinline__ PartTerms part_terms(const DevParams &P, double rho, double pr)
 {
     PartTerms t;
+    const double ir = 1.0 / rho;
     t.rho = rho;
-    t.ir = 1.0 / rho;
     t.pr = pr;
     t.c = sound_of(P, rho);
-    t.dpr = t.ir * t.ir * (t.c * t.c - 2.0 * pr * rho);
-    t.dc = 0.5 * (P.gamma - 1.0) * t.c * t.ir;
+    t.dpr = ir * ir * (t.c * t.c - 2.0 * pr * rho);
+    t.dc = 0.5 * (P.gamma - 1.0) * t.c * ir;
     return t;
 }
 
-// Terms of a pair that do not change when a and b swap (r -> -r, v -> -v):
-// the kernel factor F(r) (grad_a W = F r), (dF/dr) / r, v.r, 1/(r^2 + eta^2),
-// mu = h v.r / (r^2 + eta^2) and 1/(rho_a + rho_b).  One reciprocal square
-// root and two reciprocals; every other quotient below is a product.
-struct PairGeo {
-    double F, dFr, vdr, iden, mu, iS;
-};
-
-__device__ __forceinline__ PairGeo pair_geo(const DevParams &P, double rx, double ry, double rz,
-                                            double vx, double vy, double vz, double rho_a,
-                                            double rho_b)
+// Kernel factor of grad_a W = F r_ab and (dF/dr) / r, from one reciprocal
+// square root of r^2.
+__device__ __forceinline__ void kernel_factor(const DevParams &P, double r2, double *F,
+                                              double *dFr)
 {
-    PairGeo g;
-    const double r2 = rx * rx + ry * ry + rz * rz;
     const double irl = rsqrt(r2);
     const double q = r2 * irl * P.invh;
-    double dF;
     if (q < 1.0) {
-        g.F = P.kA64 * (-3.0 + 2.25 * q);
-        dF = P.kA64 * 2.25 * P.invh;
+        *F = P.kA64 * (-3.0 + 2.25 * q);
+        *dFr = P.kA64 * 2.25 * P.invh * irl;
     } else {
         const double t = 2.0 - q;
-        g.F = P.kB64 * t * t * irl;
-        dF = P.kB64 * (-2.0 * t * P.invh * irl - t * t * irl * irl);
+        *F = P.kB64 * t * t * irl;
+        *dFr = P.kB64 * (-2.0 * t * P.invh * irl - t * t * irl * irl) * irl;
     }
-    g.dFr = dF * irl;
-    g.vdr = vx * rx + vy * ry + vz * rz;
-    g.iden = 1.0 / (r2 + P.eta2);
-    g.mu = P.h * g.vdr * g.iden;
-    g.iS = 1.0 / (rho_a + rho_b);
-    return g;
 }
 
-// Derivatives of L = gF . f_ab + gD d_ab for the ordered pair a <- b.
-//   f_ab = -m (P_a/rho_a^2 + P_b/rho_b^2 + Pi) F r     (when momentum)
-//   d_ab = m (v_ab . r) F,   grad_a W = F r
-// r and v are r_ab and v_ab of this direction; G holds the direction-free terms.
-__device__ __forceinline__ void pair_vjp(const DevParams &P, bool momentum, const PairGeo &G,
-                                         double rx, double ry, double rz, double vx, double vy,
-                                         double vz, const PartTerms &A, const PartTerms &B,
-                                         double gFx, double gFy, double gFz, double gD,
-                                         PairGrad &g)
+// Both ordered pairs of {a, b} at once, as seen by a (self).  For the ordered
+// pair a <- b,
+//   L_ab = gF_a . f_ab + gD_a d_ab,
+//   f_ab = -m Q F r,  Q = P_a/rho_a^2 + P_b/rho_b^2 + Pi,  d_ab = m (v.r) F,
+// with r = r_ab, v = v_ab, grad_a W = F r, Pi = K mu (K = -alpha (c_a + c_b) /
+// (rho_a + rho_b), mu = h v.r / (r^2 + eta^2), only where v.r < 0).  L_ba is
+// the same function of r_ba = -r and v_ba = -v, under which F, v.r, mu and Q
+// do not change and grad_r F = (dF/dr / r) r, dQ/dr = kv v + kr r (kv = K h /
+// (r^2 + eta^2), kr = -2 kv v.r / (r^2 + eta^2)) change sign.  So
+//   d(L_ab + L_ba)/dx_a = m (gD_a + gD_b) (F v + v.r grad_r F)
+//                         - m Q (dG.r) grad_r F - m Q F dG - m F (dG.r) dQ/dr,
+//   d(L_ab + L_ba)/dv_a = (m (gD_a + gD_b) F - m F (dG.r) kv) r,
+//   d(L_ab + L_ba)/drho_a = -m F (dG.r) (d(P/rho^2)/drho_a + dPi/drho_a),
+// with dG = gF_a - gF_b (gF_b = 0 where b is a boundary particle: its pair
+// b <- a has no momentum term).  dJ/dalpha takes L_ab only, so that every
+// ordered pair counts once over all targets.  One reciprocal square root and
+// one reciprocal d = 1/((r^2 + eta^2)(rho_a + rho_b)) per pair; every other
+// quotient is a product.
+template <bool FLUID_B>
+__device__ __forceinline__ void pair_adj(const DevParams &P, double rx, double ry, double rz,
+                                         double vx, double vy, double vz, const PartTerms &A,
+                                         double rho_b, double pr_b, double c_b, double gFax,
+                                         double gFay, double gFaz, double gFbx, double gFby,
+                                         double gFbz, double gDs, SelfAdj &l)
 {
     const double m = P.mass;
-    const double F = G.F, vdr = G.vdr, mu = G.mu;
-    const double gx = G.dFr * rx, gy = G.dFr * ry, gz = G.dFr * rz;  // grad_r F
-    // continuity
-    const double cg = gD * m;
-    g.rx = cg * (F * vx + vdr * gx);
-    g.ry = cg * (F * vy + vdr * gy);
-    g.rz = cg * (F * vz + vdr * gz);
-    g.vx = cg * F * rx;
-    g.vy = cg * F * ry;
-    g.vz = cg * F * rz;
-    g.rho_a = 0.0;
-    g.rho_b = 0.0;
-    g.alpha = 0.0;
-    if (!momentum) return;
-    const double sF = gFx * rx + gFy * ry + gFz * rz;
-    const double cs = A.c + B.c;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    double F, dFr;
+    kernel_factor(P, r2, &F, &dFr);
+    const double vdr = vx * rx + vy * ry + vz * rz;
+    const double den = r2 + P.eta2, S = A.rho + rho_b;
+    const double d = 1.0 / (den * S);
+    const double iden = d * S, iS = d * den;
+    const double mu = P.h * vdr * iden;
+    const double dGx = FLUID_B ? gFax - gFbx : gFax;
+    const double dGy = FLUID_B ? gFay - gFby : gFay;
+    const double dGz = FLUID_B ? gFaz - gFbz : gFaz;
+    const double s1 = gFax * rx + gFay * ry + gFaz * rz;
+    const double sd = dGx * rx + dGy * ry + dGz * rz;
+    const double cs = A.c + c_b;
     double K = 0.0, Pi = 0.0;
     if (vdr < 0.0) {
-        K = -P.alpha * cs * G.iS;
+        K = -P.alpha * cs * iS;
         Pi = K * mu;
     }
-    const double Q = A.pr + B.pr + Pi;
-    // L_m = -m Q F sF
-    const double Aq = -m * Q * sF;   // times grad_r F
-    const double Bc = -m * Q * F;    // times gF
-    const double Cc = -m * F * sF;   // times dQ
-    // dPi/dr = K (h v / den - 2 h vdr r / den^2),  dPi/dv = K h r / den
-    const double kv = K * P.h * G.iden, kr = -2.0 * K * P.h * vdr * G.iden * G.iden;
-    g.rx += Aq * gx + Bc * gFx + Cc * (kv * vx + kr * rx);
-    g.ry += Aq * gy + Bc * gFy + Cc * (kv * vy + kr * ry);
-    g.rz += Aq * gz + Bc * gFz + Cc * (kv * vz + kr * rz);
-    g.vx += Cc * kv * rx;
-    g.vy += Cc * kv * ry;
-    g.vz += Cc * kv * rz;
-    double dPi_a = 0.0, dPi_b = 0.0;
+    const double Q = A.pr + pr_b + Pi;
+    const double mF = m * F;
+    const double cg = m * gDs;       // continuity, both directions
+    const double Aq = -m * Q * sd;   // times grad_r F
+    const double Bc = -mF * Q;       // times dG
+    const double Cc = -mF * sd;      // times dQ
+    const double kv = K * P.h * iden, kr = -2.0 * kv * vdr * iden;
+    const double gx = dFr * rx, gy = dFr * ry, gz = dFr * rz;  // grad_r F
+    l.rx += cg * (F * vx + vdr * gx) + Aq * gx + Bc * dGx + Cc * (kv * vx + kr * rx);
+    l.ry += cg * (F * vy + vdr * gy) + Aq * gy + Bc * dGy + Cc * (kv * vy + kr * ry);
+    l.rz += cg * (F * vz + vdr * gz) + Aq * gz + Bc * dGz + Cc * (kv * vz + kr * rz);
+    const double cvv = cg * F + Cc * kv;
+    l.vx += cvv * rx;
+    l.vy += cvv * ry;
+    l.vz += cvv * rz;
+    double dPi = 0.0;
     if (vdr < 0.0) {
-        const double iS2 = G.iS * G.iS;
-        dPi_a = -P.alpha * mu * (A.dc * G.iS - cs * iS2);
-        dPi_b = -P.alpha * mu * (B.dc * G.iS - cs * iS2);
-        g.alpha = Cc * (-cs * mu * G.iS);
+        dPi = -P.alpha * mu * (A.dc * iS - cs * iS * iS);
+        l.alpha += mF * s1 * cs * mu * iS;   // (-m F s1) (-(c_a + c_b) mu / (rho_a + rho_b))
     }
-    g.rho_a = Cc * (A.dpr + dPi_a);
-    g.rho_b = Cc * (B.dpr + dPi_b);
+    l.rho += Cc * (A.dpr + dPi);
+}
+
+// d L_ab / d rho_b for the ordered pair a <- b (a fluid, b the boundary
+// target): -m F (gF_a . r) (d(P/rho^2)/drho_b + dPi/drho_b).
+__device__ __forceinline__ double pair_adj_rho_b(const DevParams &P, double rx, double ry,
+                                                 double rz, double vx, double vy, double vz,
+                                                 const PartTerms &B, double rho_a, double c_a,
+                                                 double gFx, double gFy, double gFz)
+{
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    double F, dFr;
+    kernel_factor(P, r2, &F, &dFr);
+    const double Cc = -P.mass * F * (gFx * rx + gFy * ry + gFz * rz);
+    const double vdr = vx * rx + vy * ry + vz * rz;
+    double dPi = 0.0;
+    if (vdr < 0.0) {
+        const double den = r2 + P.eta2, S = rho_a + B.rho;
+        const double d = 1.0 / (den * S);
+        const double iS = d * den, mu = P.h * vdr * d * S;
+        const double cs = c_a + B.c;
+        dPi = -P.alpha * mu * (B.dc * iS - cs * iS * iS);
+    }
+    return Cc * (B.dpr + dPi);
 }
 
 __device__ __forceinline__ void cell_coords(const DevParams &P, uint32_t c, int *cx, int *cy,
@@ -316,11 +337,10 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
         const PartTerms ta = part_terms(P, va.w, pa.w);
         const double gFx = gF[3 * (size_t)i], gFy = gF[3 * (size_t)i + 1],
                      gFz = gF[3 * (size_t)i + 2], gDa = gD[i];
-        double lx = 0, ly = 0, lz = 0, lvx = 0, lvy = 0, lvz = 0, lr = 0;
+        SelfAdj l = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
         const double s2 = 4.0 * P.h * P.h;
         int cx, cy, cz;
         cell_coords(P, cell[i], &cx, &cy, &cz);
-        PairGrad g;
         const float4 fa = posf[i];
         // fluid neighbours: F-F in both directions
         FOR_RUNS_F(P, cx, cy, cz, fstart, fa, posf, j, {
@@ -330,21 +350,9 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
             const double r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < s2)) continue;
             const double4_32a vb = velr[j];
-            const PartTerms tb = part_terms(P, vb.w, pb.w);
-            const double vx = va.x - vb.x, vy = va.y - vb.y, vz = va.z - vb.z;
-            const PairGeo G = pair_geo(P, rx, ry, rz, vx, vy, vz, ta.rho, tb.rho);
-            // self receives from j
-            pair_vjp(P, true, G, rx, ry, rz, vx, vy, vz, ta, tb, gFx, gFy, gFz, gDa, g);
-            lx += g.rx; ly += g.ry; lz += g.rz;
-            lvx += g.vx; lvy += g.vy; lvz += g.vz;
-            lr += g.rho_a;
-            dal += g.alpha;
-            // j receives from self (r_ji = -r, v_ji = -v)
-            pair_vjp(P, true, G, -rx, -ry, -rz, -vx, -vy, -vz, tb, ta, gF[3 * (size_t)j],
-                     gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gD[j], g);
-            lx -= g.rx; ly -= g.ry; lz -= g.rz;
-            lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
-            lr += g.rho_b;
+            pair_adj<true>(P, rx, ry, rz, va.x - vb.x, va.y - vb.y, va.z - vb.z, ta, vb.w, pb.w,
+                           sound_of(P, vb.w), gFx, gFy, gFz, gF[3 * (size_t)j],
+                           gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gDa + gD[j], l);
         })
         // boundary neighbours: F-B (momentum + continuity) and B-F (continuity)
         FOR_RUNS_F(P, cx, cy, cz, bstart, fa, bposf, j, {
@@ -352,24 +360,15 @@ k_adj_pi_fluid(int nf, size_t N, DevParams P, const double4_32a *__restrict__ po
             const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
             const double r2 = rx * rx + ry * ry + rz * rz;
             if (!(r2 < s2)) continue;
-            const double4_32a vb = bvelr[j];
-            const PartTerms tb = part_terms(P, vb.w, pb.w);
-            const double vx = va.x, vy = va.y, vz = va.z;
-            const PairGeo G = pair_geo(P, rx, ry, rz, vx, vy, vz, ta.rho, tb.rho);
-            pair_vjp(P, true, G, rx, ry, rz, vx, vy, vz, ta, tb, gFx, gFy, gFz, gDa, g);
-            lx += g.rx; ly += g.ry; lz += g.rz;
-            lvx += g.vx; lvy += g.vy; lvz += g.vz;
-            lr += g.rho_a;
-            dal += g.alpha;
-            pair_vjp(P, false, G, -rx, -ry, -rz, -vx, -vy, -vz, tb, ta, 0.0, 0.0, 0.0,
-                     gD[(size_t)nf + j], g);
-            lx -= g.rx; ly -= g.ry; lz -= g.rz;
-            lvx -= g.vx; lvy -= g.vy; lvz -= g.vz;
+            const double rho_b = bvelr[j].w;
+            pair_adj<false>(P, rx, ry, rz, va.x, va.y, va.z, ta, rho_b, pb.w, sound_of(P, rho_b),
+                            gFx, gFy, gFz, 0.0, 0.0, 0.0, gDa + gD[(size_t)nf + j], l);
         })
+        dal = l.alpha;
         double *ox = lam_s + 3 * (size_t)i, *ov = lam_s + 3 * N + 3 * (size_t)i;
-        ox[0] += lx; ox[1] += ly; ox[2] += lz;
-        ov[0] += lvx; ov[1] += lvy; ov[2] += lvz;
-        lam_s[6 * N + i] += lr;
+        ox[0] += l.rx; ox[1] += l.ry; ox[2] += l.rz;
+        ov[0] += l.vx; ov[1] += l.vy; ov[2] += l.vz;
+        lam_s[6 * N + i] += l.rho;
     }
     // deterministic block sum of dJ/dalpha
     for (int o = 16; o > 0; o >>= 1) dal += __shfl_xor_sync(0xffffffffu, dal, o);
@@ -400,7 +399,6 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
     int cx, cy, cz;
     cell_coords(P, bcell[j], &cx, &cy, &cz);
     double lr = 0.0;
-    PairGrad g;
     const float4 fb = bposf[j];
     FOR_RUNS_F(P, cx, cy, cz, fstart, fb, posf, i, {
         const double4_32a pa = posp[i];
@@ -408,11 +406,8 @@ k_adj_pi_boundary(int nf, int nb, size_t N, DevParams P, const double4_32a *__re
         const double r2 = rx * rx + ry * ry + rz * rz;
         if (!(r2 < s2)) continue;
         const double4_32a va = velr[i];
-        const PartTerms ta = part_terms(P, va.w, pa.w);
-        const PairGeo G = pair_geo(P, rx, ry, rz, va.x, va.y, va.z, ta.rho, tb.rho);
-        pair_vjp(P, true, G, rx, ry, rz, va.x, va.y, va.z, ta, tb, gF[3 * (size_t)i],
-                 gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2], gD[i], g);
-        lr += g.rho_b;
+        lr += pair_adj_rho_b(P, rx, ry, rz, va.x, va.y, va.z, tb, va.w, sound_of(P, va.w),
+                             gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2]);
     })
     lam_s[6 * N + (size_t)nf + j] += lr;
 }

@@ -70,19 +70,25 @@ __device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa
     double F = q < 1.0 ? P.kA64 * (-3.0 + 2.25 * q) : P.kB64 * (2.0 - q) * (2.0 - q) * rinv;
     double dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
     double vdr = dvx * rx + dvy * ry + dvz * rz;
-    double mu = P.h * vdr / (r2 + P.eta2);
+    double mu;
     if (MOMENTUM) {
+        // one reciprocal for both quotients: d = 1/((r^2 + eta^2)(rho_a + rho_b))
+        const double S = va.w + vb.w, hv = P.h * vdr;
+        const double d = 1.0 / ((r2 + P.eta2) * S);
+        mu = hv * S * d;
         double Pi = 0.0;
         if (vdr < 0.0) {
             double rb = vb.w * P.inv_rho0;
             double cb = P.gamma_is_7 ? P.c0 * rb * rb * rb : P.c0 * pow(rb, 0.5 * (P.gamma - 1.0));
-            Pi = -P.alpha * (ca + cb) * mu / (va.w + vb.w);
+            Pi = -P.alpha * (ca + cb) * hv * d;
         }
         if (P.tensile) Pi += tensile64(P, q, pa.w, pb.w);
         double coef = -(pa.w + pb.w + Pi) * F;
         o.ax += coef * rx;
         o.ay += coef * ry;
         o.az += coef * rz;
+    } else {
+        mu = P.h * vdr / (r2 + P.eta2);
     }
     o.ar += vdr * F;
     o.vis = fmax(o.vis, fabs(mu));
