@@ -27,9 +27,10 @@
 // most 32 particles together (a boundary cell holds about 10), the candidates
 // being the fluid of the union of their neighbourhoods (x-runs from the first
 // cell - 1 to the last + 1); each candidate is shifted by its own cell's x
-// distance from the first cell, each target by its cell's.  Sums of
-// a target are accumulated by one lane in candidate order, so results do not
-// depend on the order the items are processed in.
+// distance from the first cell, each target by its cell's.  Fluid and boundary
+// items form one queue (fluid first) served by one launch.  Sums of a target
+// are accumulated by one lane in candidate order, so results do not depend on
+// the order the items are processed in.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -42,8 +43,11 @@
 #ifndef SPH_PI_WARPS
 #define SPH_PI_WARPS 4
 #endif
+// Resident CTAs per SM the register allocation is held to: shared memory
+// (about 42.7 KB per CTA) admits 5 per SM, and 5 CTAs of 128 threads need at
+// most 96 registers per thread.
 #ifndef SPH_PI_MINB
-#define SPH_PI_MINB 1
+#define SPH_PI_MINB 5
 #endif
 
 namespace sph {
@@ -143,35 +147,23 @@ __device__ __forceinline__ void pair(const DevParams &P, float xa, float ya, flo
     o.vis = fmaxf(o.vis, fabsf(mu));
 }
 
-// MOMENTUM: fluid targets (F-F and F-B, acc out).  !MOMENTUM: boundary targets
-// (B-F continuity only, bar out).
+// One work item, processed by the whole warp.  MOMENTUM: fluid targets (F-F
+// and F-B, acc out).  !MOMENTUM: boundary targets (B-F continuity only, bar
+// out).  t* are the target arrays, f* the fluid candidates, b* the boundary
+// candidates (fluid targets only).
 template <bool MOMENTUM, bool TENSILE>
-__global__ void __launch_bounds__(WARPS * 32, SPH_PI_MINB)
-k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restrict__ n_items_p,
-       uint32_t *__restrict__ next_p, const float4 *__restrict__ tposp,
-       const float4 *__restrict__ tvelr, const uint32_t *__restrict__ tcell,
-       const int32_t *__restrict__ tstart, const float4 *__restrict__ fposp,
-       const float4 *__restrict__ fvelr, const int32_t *__restrict__ fstart,
-       const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
-       const int32_t *__restrict__ bstart, float4 *__restrict__ acc, float *__restrict__ bar,
-       const uint32_t *__restrict__ fcell, Scalars *sc)
+__device__ __forceinline__ void pi32_item(
+    const DevParams &P, WarpSmem &S, int lane, uint32_t it, const uint32_t *__restrict__ items,
+    const float4 *__restrict__ tposp, const float4 *__restrict__ tvelr,
+    const uint32_t *__restrict__ tcell, const int32_t *__restrict__ tstart,
+    const float4 *__restrict__ fposp, const float4 *__restrict__ fvelr,
+    const int32_t *__restrict__ fstart, const float4 *__restrict__ bposp,
+    const float4 *__restrict__ bvelr, const int32_t *__restrict__ bstart,
+    float4 *__restrict__ acc, float *__restrict__ bar, const uint32_t *__restrict__ fcell,
+    double &f2max, float &vismax, bool &bad)
 {
-    __shared__ WarpSmem smem[WARPS];
-    __shared__ double red[32];
-    const int lane = threadIdx.x & 31;
-    WarpSmem &S = smem[threadIdx.x >> 5];
-    const uint32_t n_items = *n_items_p;
-    double f2max = 0.0;
-    float vismax = 0.0f;
-    bool bad = false;
     const int nlists = MOMENTUM ? 2 : 1;
-
-    for (;;) {
-        uint32_t it = 0;
-        if (lane == 0) it = atomicAdd(next_p, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if (it >= n_items) break;
-
+    {
         // ---- the item: fluid targets [i0, i0 + nt) of cell c; boundary
         // targets [i0, i0 + nt) of cells c .. c + (cx1 - cx) of one x row
         int i0, nt;
@@ -337,8 +329,47 @@ k_pi32(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__restri
             vismax = fmaxf(vismax, o.vis);
         }
     }
+}
+
+// PI over one queue of work items: the nf_items fluid items first (F-F + F-B),
+// then the nb_items packed boundary items (B-F), taken by the warps of a
+// persistent grid from one atomic counter, so that boundary items fill the
+// tail of the fluid work instead of following it in a second launch.
+template <bool TENSILE>
+__global__ void __launch_bounds__(WARPS * 32, SPH_PI_MINB)
+k_pi32(DevParams P, const uint32_t *__restrict__ items_f, const uint32_t *__restrict__ items_b,
+       const uint32_t *__restrict__ ctr, int use_b, uint32_t *__restrict__ next_p,
+       const float4 *__restrict__ posp, const float4 *__restrict__ velr,
+       const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
+       const float4 *__restrict__ bposp, const float4 *__restrict__ bvelr,
+       const uint32_t *__restrict__ bcell, const int32_t *__restrict__ bstart,
+       float4 *__restrict__ acc, float *__restrict__ bar, Scalars *sc)
+{
+    __shared__ WarpSmem smem[WARPS];
+    __shared__ double red[32];
+    const int lane = threadIdx.x & 31;
+    WarpSmem &S = smem[threadIdx.x >> 5];
+    const uint32_t nfi = ctr[0];
+    const uint32_t n_items = nfi + (use_b ? ctr[3] : 0u);
+    double f2max = 0.0;
+    float vismax = 0.0f;
+    bool bad = false;
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(next_p, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        if (it < nfi)
+            pi32_item<true, TENSILE>(P, S, lane, it, items_f, posp, velr, cell, fstart, posp,
+                                     velr, fstart, bposp, bvelr, bstart, acc, bar, cell, f2max,
+                                     vismax, bad);
+        else
+            pi32_item<false, false>(P, S, lane, it - nfi, items_b, bposp, bvelr, bcell, bstart,
+                                    posp, velr, fstart, nullptr, nullptr, bstart, acc, bar, cell,
+                                    f2max, vismax, bad);
+    }
     if (bad) atomicOr(&sc->flags, SPH_FLAG_NAN);
-    if (MOMENTUM) block_max_to(&sc->mx.f2, f2max, red);
+    block_max_to(&sc->mx.f2, f2max, red);
     block_max_to(&sc->mx.visc, (double)vismax, red);
 }
 
@@ -388,23 +419,19 @@ __global__ void k_pack_boundary_items(DevParams P, const uint32_t *__restrict__ 
 
 int pi32_setup(sph_ctx *ctx)
 {
-    int dev = 0, sms = 0, bf = 0, bb = 0;
+    int dev = 0, sms = 0, nblk = 0;
     if (check_cuda(cudaGetDevice(&dev))) return SPH_ERR_CUDA;
     if (check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
         return SPH_ERR_CUDA;
     if (ctx->dp.tensile) {
-        if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true, true>,
+        if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_pi32<true>,
                                                                     WARPS * 32, 0)))
             return SPH_ERR_CUDA;
-    } else if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_pi32<true, false>,
+    } else if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_pi32<false>,
                                                                        WARPS * 32, 0))) {
         return SPH_ERR_CUDA;
     }
-    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bb, k_pi32<false, false>,
-                                                                WARPS * 32, 0)))
-        return SPH_ERR_CUDA;
-    ctx->pi_grid_f = sms * (bf > 0 ? bf : 1);
-    ctx->pi_grid_b = sms * (bb > 0 ? bb : 1);
+    ctx->pi_grid_f = sms * (nblk > 0 ? nblk : 1);
     return SPH_OK;
 }
 
@@ -424,30 +451,22 @@ int pi32_launch(sph_ctx *ctx)
 {
     Workspace &w = ctx->w;
     cudaStream_t st = ctx->stream;
-    // clear the two "next item" counters (fluid, boundary)
-    if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, 2 * sizeof(uint32_t), st))) return SPH_ERR_CUDA;
-    if (ctx->nf > 0) {
-        if (ctx->dp.tensile)
-            SPH_LAUNCH(ctx, (k_pi32<true, true>), ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp,
-                       w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
-                       (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
-                       (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
-                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr,
-                       w.cell, w.sc);
-        else
-            SPH_LAUNCH(ctx, (k_pi32<true, false>), ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp,
-                       w.items_f, &w.ctr[0], &w.ctr[1], (const float4 *)w.posp,
-                       (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.posp,
-                       (const float4 *)w.velr, w.fstart, (const float4 *)w.bposp,
-                       (const float4 *)w.bvelr, w.bstart, (float4 *)w.acc, (float *)nullptr,
-                       w.cell, w.sc);
-    }
-    if (ctx->nb > 0)
-        SPH_LAUNCH(ctx, (k_pi32<false, false>), ctx->pi_grid_b, WARPS * 32, 0, st, ctx->dp, w.items_b,
-                   &w.ctr[3], &w.ctr[2], (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell,
-                   w.bstart, (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
-                   (const float4 *)nullptr, (const float4 *)nullptr, w.bstart, (float4 *)nullptr,
-                   (float *)w.bar, w.cell, w.sc);
+    if (ctx->nf == 0 && ctx->nb == 0) return SPH_OK;
+    // clear the "next item" counter of the queue
+    if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, sizeof(uint32_t), st))) return SPH_ERR_CUDA;
+    const int use_b = ctx->nb > 0 ? 1 : 0;
+    if (ctx->dp.tensile)
+        SPH_LAUNCH(ctx, k_pi32<true>, ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp, w.items_f,
+                   w.items_b, w.ctr, use_b, &w.ctr[1], (const float4 *)w.posp,
+                   (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.bposp,
+                   (const float4 *)w.bvelr, w.bcell, w.bstart, (float4 *)w.acc, (float *)w.bar,
+                   w.sc);
+    else
+        SPH_LAUNCH(ctx, k_pi32<false>, ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp, w.items_f,
+                   w.items_b, w.ctr, use_b, &w.ctr[1], (const float4 *)w.posp,
+                   (const float4 *)w.velr, w.cell, w.fstart, (const float4 *)w.bposp,
+                   (const float4 *)w.bvelr, w.bcell, w.bstart, (float4 *)w.acc, (float *)w.bar,
+                   w.sc);
     return check_cuda(cudaGetLastError());
 }
 

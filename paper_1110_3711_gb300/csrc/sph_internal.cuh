@@ -123,7 +123,7 @@ struct sph_ctx {
     bool nl_valid, pi_valid;
     long long launches;
     int device;
-    int pi_grid_f, pi_grid_b;   // persistent grid sizes of the FP32 PI kernels
+    int pi_grid_f;              // persistent grid size of the FP32 warp PI kernels
     bool branges_ready;         // boundary x-run table built for the current boundary list
     bool boundary_built;        // the boundary list exists (built at least once)
     // sph_run_graph: executable graphs of two consecutive steps, one per value
