@@ -1,19 +1,21 @@
 // NL stage (Sections 2 and 4.1 of the paper): cell-linked list on the GPU.
 //
+// Fluid (every step), a counting sort by cell:
 //   k_hash        cell of every particle: c_d = floor((x_d - min_d) / s), linear
-//                 id cx + nx (cy + ny cz) (cells follow X, Y, Z; Section 4.4);
-//                 keys and source positions are scattered to persistent-id
-//                 order, so that the stable sort below yields the (cell, id)
-//                 order no matter how the particles were ordered before.
-//   radix sort    stable LSD, 8-bit digits: k_radix_hist (tile histograms),
-//                 exclusive scan (digit-major), k_radix_scatter (ranks from
-//                 warp match + per-warp digit counters, no atomics, stable).
-//   k_reorder     gather of every fluid array into the sorted order, plus the
-//                 packed PI inputs of Section 4.3 {pos, P/rho^2}, {vel, rho}
-//                 and the largest sound speed (Section 4.1 maxima).
+//                 id cx + nx (cy + ny cz) (cells follow X, Y, Z; Section 4.4),
+//                 the per-cell counts and a slot inside the cell (atomics).
 //   cell starts   exclusive scan of the per-cell counts: start[c] = number of
 //                 particles in cells below c, i.e. CellBeginEnd of Fig. 8 with
 //                 empty cells as equal begin and end.
+//   k_place       cell-grouped order start[c] + slot (arbitrary inside a cell).
+//   k_reorder     rank by id inside the cell, which gives the (cell, id) order
+//                 whatever the order before; copy of every fluid array to that
+//                 place, plus the packed PI inputs of Section 4.3 {pos, P/rho^2},
+//                 {vel, rho} and the largest sound speed (Section 4.1 maxima).
+// Boundary (once) and the static entry point: a stable LSD radix sort of the
+// keys in id order, 8-bit digits: k_radix_hist (tile histograms), exclusive
+// scan (digit-major), k_radix_scatter (ranks from warp match + per-warp digit
+// counters, no atomics, stable).
 // All kernels are HBM-bound; grids are sized from the particle count.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -82,26 +84,46 @@ __device__ __forceinline__ uint32_t cell_of(const DevParams &P, double x, double
     return (uint32_t)cx + (uint32_t)P.nx * ((uint32_t)cy + (uint32_t)P.ny * (uint32_t)cz);
 }
 
-// One thread per particle (current order i).  key_by_id[id - id_base] = cell,
-// val_by_id[id - id_base] = i; count[cell] += 1.
+// One thread per particle (current order i): its cell (cell_i[i]), its slot
+// among the particles of that cell (slot_i[i]) and count[cell] += 1.  The
+// slots come from one atomic per distinct cell of the warp (consecutive
+// particles mostly share a cell), so their order inside a cell is arbitrary;
+// k_reorder restores the id order inside every cell.
 __global__ void k_hash(const double *__restrict__ x, const double *__restrict__ y,
-                       const double *__restrict__ z, const uint32_t *__restrict__ id,
-                       uint32_t id_base, int n, DevParams P, uint32_t *__restrict__ key_by_id,
-                       uint32_t *__restrict__ val_by_id, uint32_t *__restrict__ count,
-                       Scalars *sc)
+                       const double *__restrict__ z, int n, DevParams P,
+                       uint32_t *__restrict__ cell_i, uint32_t *__restrict__ slot_i,
+                       uint32_t *__restrict__ count, Scalars *sc)
 {
-    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31;
     // lanes past the end take a key no particle has, so the warp stays whole
-    uint32_t c = i < n ? cell_of(P, x[i], y[i], z[i]) : 0xffffffffu;
+    const uint32_t c = i < n ? cell_of(P, x[i], y[i], z[i]) : 0xffffffffu;
+    const unsigned peers = __match_any_sync(0xffffffffu, c);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (i < n && lane == leader) base = atomicAdd(&count[c], (uint32_t)__popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
     if (i < n) {
-        uint32_t k = id ? id[i] - id_base : (uint32_t)i;
-        key_by_id[k] = c;
-        val_by_id[k] = (uint32_t)i;
+        cell_i[i] = c;
+        slot_i[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+        if (c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
     }
-    // consecutive particles share a cell: one atomic per distinct cell of the warp
-    unsigned peers = __match_any_sync(0xffffffffu, c);
-    if (i < n && (threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&count[c], (uint32_t)__popc(peers));
-    if (i < n && c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
+}
+
+// One thread per particle (current order i): position q = start[cell] + slot in
+// the cell-grouped order; cell_q[q] = cell, src_q[q] = i, id_q[q] = id.
+__global__ void k_place(int n, const uint32_t *__restrict__ cell_i,
+                        const uint32_t *__restrict__ slot_i, const uint32_t *__restrict__ id,
+                        const int32_t *__restrict__ start, uint32_t *__restrict__ cell_q,
+                        uint32_t *__restrict__ src_q, uint32_t *__restrict__ id_q)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint32_t c = cell_i[i];
+    const uint32_t q = (uint32_t)start[c] + slot_i[i];
+    cell_q[q] = c;
+    src_q[q] = (uint32_t)i;
+    id_q[q] = id[i];
 }
 
 // ------------------------------------------------------------- radix sort --
@@ -388,14 +410,19 @@ __device__ __forceinline__ void cell_origin(const DevParams &P, const double *__
     *oz = origin[P.nx + P.ny + cz];
 }
 
-// Threads [0, nf): gather fluid arrays from buffer `src` to buffer `dst` in the
-// sorted order and write the packed PI inputs.  Threads [nf, nf+nb): refresh
-// the packed pressure/density of boundary particle (i - nf).  Block max of the
-// sound speed goes to sc->mx.c.
+// Threads [0, nf): particle q of the cell-grouped order (cell_q, src_q, id_q
+// from k_place) takes position p = start[c] + (number of particles of its cell
+// with a smaller id), which is its place in the (cell, id) order; its fluid
+// arrays are copied from buffer `src` to position p of buffer `dst` with the
+// packed PI inputs.  The ids of a cell are contiguous in id_q, so the rank
+// reads them from L1 (about 27 per cell at rest density; the cost grows with
+// the square of a cell's population).  Threads [nf, nf+nb): refresh the packed
+// pressure/density of boundary particle (i - nf).  Block max of the sound
+// speed goes to sc->mx.c.
 template <typename Real, bool SPLIT>
 __global__ void __launch_bounds__(256)
-k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
-          const uint32_t *__restrict__ val_sorted,
+k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
+          const uint32_t *__restrict__ src_q, const uint32_t *__restrict__ id_q,
           const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
           const Real *__restrict__ svx, const Real *__restrict__ svy, const Real *__restrict__ svz,
           const Real *__restrict__ svmx, const Real *__restrict__ svmy, const Real *__restrict__ svmz,
@@ -418,20 +445,27 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
     // the largest sound speed, in the precision of the form
     Real cmax = 0;
     bool item = false;
+    int p = 0;  // destination of thread i
     if (i < nf) {
-        uint32_t s = val_sorted[i];
-        uint32_t c = key_sorted[i];
+        const uint32_t s = src_q[i];
+        const uint32_t c = cell_q[i];
+        const uint32_t myid = id_q[i];
+        const int b = fstart[c], e = fstart[c + 1];
+        int r = 0;
+#pragma unroll 4
+        for (int k = b; k < e; ++k) r += id_q[k] < myid ? 1 : 0;
+        p = b + r;
         // a PI work item starts at every 32nd particle of a cell
-        if (SPLIT && c < P.ncells) item = ((i - fstart[c]) & 31) == 0;
+        if (SPLIT && c < P.ncells) item = (r & 31) == 0;
         double x = sx[s], y = sy[s], z = sz[s];
         Real vx = svx[s], vy = svy[s], vz = svz[s];
         Real rho = srho[s];
-        dx[i] = x; dy[i] = y; dz[i] = z;
-        dvx[i] = vx; dvy[i] = vy; dvz[i] = vz;
-        dvmx[i] = svmx[s]; dvmy[i] = svmy[s]; dvmz[i] = svmz[s];
-        drho[i] = rho; drhom[i] = srhom[s];
-        did[i] = sid[s];
-        cell[i] = c;
+        dx[p] = x; dy[p] = y; dz[p] = z;
+        dvx[p] = vx; dvy[p] = vy; dvz[p] = vz;
+        dvmx[p] = svmx[s]; dvmy[p] = svmy[s]; dvmz[p] = svmz[s];
+        drho[p] = rho; drhom[p] = srhom[s];
+        did[p] = myid;
+        cell[p] = c;
         V4 pp, vv;
         if (SPLIT) {
             float pr, cs;
@@ -448,12 +482,12 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
                 cmax = (Real)cs;
                 double ox, oy, oz;
                 cell_origin(P, origin, c, &ox, &oy, &oz);
-                posf[i] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
+                posf[p] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
             }
         }
         vv.x = vx; vv.y = vy; vv.z = vz; vv.w = rho;
-        posp[i] = pp;
-        velr[i] = vv;
+        posp[p] = pp;
+        velr[p] = vv;
     } else if (i < nf + nb) {
         int j = i - nf;
         if (j < bstart[P.ncells]) {
@@ -484,7 +518,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ key_sorted,
             uint32_t base = 0;
             if (lane == 0) base = atomicAdd(&ctr[0], (uint32_t)__popc(ball));
             base = __shfl_sync(0xffffffffu, base, 0);
-            if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)i;
+            if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)p;
         }
     }
     if (SPLIT) block_max_to_f(&sc->mx.c, (float)cmax, redf);
@@ -568,20 +602,22 @@ static int nl_fluid_t(sph_ctx *ctx)
     const int T = 256;
     if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2 + kCtrReset), st)))
         return SPH_ERR_CUDA;
-    if (nf > 0) {
-        SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src],
-                   w.id[src], 0u, nf, ctx->dp, w.key_by_id, w.val_by_id, w.count, w.sc);
-        int rc = radix_sort(ctx, w.key_by_id, w.val_by_id, w.key_tmp, w.val_tmp, w.key_sorted,
-                            w.val_sorted, nf, ctx->nl_passes, st);
-        if (rc) return rc;
-    }
+    // cell and slot of every particle (key_tmp, val_tmp), counts per cell
+    if (nf > 0)
+        SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src], nf,
+                   ctx->dp, w.key_tmp, w.val_tmp, w.count, w.sc);
     int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.fstart, (int64_t)ctx->ncells + 2,
                                 w.scan_part, st);
     if (rc) return rc;
+    // cell-grouped order: cell (key_sorted), source (val_sorted), id (key_by_id)
+    if (nf > 0)
+        SPH_LAUNCH(ctx, k_place, (nf + T - 1) / T, T, 0, st, nf, w.key_tmp, w.val_tmp, w.id[src],
+                   w.fstart, w.key_sorted, w.val_sorted, w.key_by_id);
     int tot = nf + nb;
     if (tot > 0) {
         SPH_LAUNCH(ctx, (k_reorder<Real, SPLIT>), (tot + T - 1) / T, T, 0, st, nf, nb, ctx->dp,
-                   w.key_sorted, w.val_sorted, w.x[src], w.y[src], w.z[src], (const Real *)w.vx[src],
+                   w.key_sorted, w.val_sorted, w.key_by_id, w.x[src], w.y[src], w.z[src],
+                   (const Real *)w.vx[src],
                    (const Real *)w.vy[src], (const Real *)w.vz[src], (const Real *)w.vmx[src],
                    (const Real *)w.vmy[src], (const Real *)w.vmz[src], (const Real *)w.rho[src],
                    (const Real *)w.rhom[src], w.id[src], w.x[dst], w.y[dst], w.z[dst],

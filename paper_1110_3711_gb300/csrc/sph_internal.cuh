@@ -10,8 +10,10 @@
 //   PI output acc = {ax, ay, az, drho/dt} per fluid particle.
 //   boundary state (never moves, sorted once): x y z (f64), rho rhom (Real),
 //   id (u32), packed posp/velr like the fluid, ar (Real) output.
-//   NL scratch: keys/values by id, their sorted copies, per-cell counts and
-//   first indices (fluid and boundary), radix-sort tile histograms.
+//   NL scratch: cell and in-cell slot per particle, the cell-grouped cell /
+//   source / id arrays (fluid, every step); keys/values by id and their
+//   sorted copies (boundary radix sort, once); per-cell counts and first
+//   indices (fluid and boundary), radix-sort tile histograms.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -84,7 +86,9 @@ struct Workspace {
     uint32_t *bid, *bcell;
     char *bstate_chunk;
     size_t bstate_chunk_bytes;
-    // NL scratch
+    // NL scratch.  Fluid: key_tmp / val_tmp = cell / slot per particle,
+    // key_sorted / val_sorted / key_by_id = cell / source / id in the
+    // cell-grouped order.  Boundary: the radix sort's keys and values.
     uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
     uint32_t *count;          // [ncells + 2], then the work-item counters ctr
     uint32_t *ctr;            // [0] fluid items, [1] fluid next, [2] boundary next, [3] boundary items
