@@ -320,6 +320,18 @@ def traffic_from_profiles(kernel_src):
 
 # --------------------------------------------------------------- CPU legs --
 
+def measured_fma(torch):
+    """Float32 and float64 FMA rates of this GPU (sph_fma_rate: independent FMA
+    chains, CUDA events), in TFLOP/s at 2 FLOP per FMA."""
+    from paper_1110_3711_gb300 import sph
+    scratch = torch.zeros(2, dtype=torch.float64, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    out = {}
+    for name in ("fp32", "fp64"):
+        out[name + "_tflops"] = sph.sph_fma_rate(name, scratch, st) / 1e12
+    return out
+
+
 def cpu_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -507,6 +519,7 @@ def main():
         del case5
 
     pk = peaks()
+    fma = measured_fma(torch)
     clk = r32.get("clocks", {})
     flops = pi_flops(r32["counts"])
     achieved = flops / (r32["pi_ms"] / 1e3) / 1e12
@@ -534,13 +547,17 @@ def main():
                   "interactions_per_s": r64["interactions_per_s"], "steps": args.fp64_steps,
                   "stage_ms": r64["stage_ms"]}),
         "fp32_over_fp64": None if r64 is None else r32["steps_per_s"] / r64["steps_per_s"],
-        "roofline": {"bound": "alu", "kernel": "PI (sph_interact: F-F+F-B and B-F kernels)",
+        "roofline": {"bound": "alu",
+                     "kernel": "PI (sph_interact: k_pi32, fluid and boundary work items)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_source": "152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (derived)",
                      "flops_per_call": flops,
                      "frac_at_measured_clock": (achieved / fp32_peak_tflops(clk["sm_mhz"])
-                                                if clk.get("sm_mhz") else None)},
+                                                if clk.get("sm_mhz") else None),
+                     "frac_of_measured_fma": (achieved / fma["fp32_tflops"]
+                                              if fma.get("fp32_tflops") else None)},
+        "measured_fma": fma,
         "e2e": e2e,
         "gpu_launches": g["launches"] if g else r32["launches"],
         "clocks": clk,

@@ -302,6 +302,19 @@ int sph_neighbour_list_static(const sph_params *p, int64_t n, const double *pos,
                               uint32_t *sorted_id, uint32_t *cell, int32_t *cell_start,
                               void *stream);
 
+/* Measurement helper, not part of the method: the rate of independent fused
+ * multiply-adds on the current device, i.e. the arithmetic roofline of PI
+ * (float32 FMAs for SPH_FP32_SPLIT, float64 FMAs for SPH_FP64).  One warm-up
+ * and one timed launch of a kernel of 8 independent FMA chains per thread and
+ * 2048 threads per SM, timed with CUDA events on `stream` (about 10 ms).
+ *   precision  SPH_FP32_SPLIT or SPH_FP64, else SPH_ERR_INVALID_ARG
+ *   scratch    device memory of at least 8 bytes that the caller owns (written
+ *              only if the chains reached a value they cannot reach)
+ *   stream     CUDA stream (NULL: legacy default stream)
+ *   flops      out: 2 x FMAs per second (host)
+ * Synchronises the stream. */
+int sph_fma_rate(int precision, void *scratch, void *stream, double *flops);
+
 /* Human-readable text of a return code (static storage). */
 const char *sph_error_string(int code);
 

@@ -450,6 +450,11 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
         const uint32_t s = src_q[i];
         const uint32_t c = cell_q[i];
         const uint32_t myid = id_q[i];
+        // the source loads are issued before the rank loop, which hides their latency
+        const double x = sx[s], y = sy[s], z = sz[s];
+        const Real vx = svx[s], vy = svy[s], vz = svz[s];
+        const Real vmx = svmx[s], vmy = svmy[s], vmz = svmz[s];
+        const Real rho = srho[s], rhom = srhom[s];
         const int b = fstart[c], e = fstart[c + 1];
         int r = 0;
 #pragma unroll 4
@@ -457,13 +462,10 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
         p = b + r;
         // a PI work item starts at every 32nd particle of a cell
         if (SPLIT && c < P.ncells) item = (r & 31) == 0;
-        double x = sx[s], y = sy[s], z = sz[s];
-        Real vx = svx[s], vy = svy[s], vz = svz[s];
-        Real rho = srho[s];
         dx[p] = x; dy[p] = y; dz[p] = z;
         dvx[p] = vx; dvy[p] = vy; dvz[p] = vz;
-        dvmx[p] = svmx[s]; dvmy[p] = svmy[s]; dvmz[p] = svmz[s];
-        drho[p] = rho; drhom[p] = srhom[s];
+        dvmx[p] = vmx; dvmy[p] = vmy; dvmz[p] = vmz;
+        drho[p] = rho; drhom[p] = rhom;
         did[p] = myid;
         cell[p] = c;
         V4 pp, vv;

@@ -18,6 +18,7 @@ from . import build as _build
 
 SPH_FP64 = 0
 SPH_FP32_SPLIT = 1
+PRECISIONS = {"fp64": SPH_FP64, "fp32": SPH_FP32_SPLIT, "fp32_split": SPH_FP32_SPLIT}
 PI_KERNELS = {"warp": 0, "thread": 1, "thread_fastcells": 2, "warp_sym": 3}
 FLAG_OUT_OF_GRID = 1
 FLAG_NAN = 2
@@ -48,8 +49,7 @@ class sph_params(C.Structure):
 
 def make_params(run_params, precision, pi_kernel="warp") -> sph_params:
     """Fill ``sph_params`` from any object with the same field names."""
-    prec = {"fp64": SPH_FP64, "fp32": SPH_FP32_SPLIT, "fp32_split": SPH_FP32_SPLIT}.get(
-        precision, precision)
+    prec = PRECISIONS.get(precision, precision)
     p = sph_params()
     for name in ("dp", "h", "cell_size", "rho0", "gamma", "c0", "alpha", "eta2_coef", "cfl",
                  "mass", "fixed_dt"):
@@ -105,6 +105,7 @@ def lib():
                 "sph_save_state": ([vp, vp], i32),
                 "sph_load_state": ([vp, vp], i32),
                 "sph_neighbour_list_static": ([pp, i64, vp, vp, vp, vp, vp], i32),
+                "sph_fma_rate": ([i32, vp, vp, C.POINTER(C.c_double)], i32),
                 "sph_sensor_pressure": ([vp, vp, i64, vp], i32),
                 "sph_sensor_adjoint": ([vp, vp, i64, vp, vp], i32),
                 "sph_front_position": ([vp, C.c_double, vp], i32),
@@ -129,7 +130,7 @@ def exported_symbols():
             "sph_count_work", "sph_launch_count", "sph_checkpoint_bytes", "sph_save_state",
             "sph_load_state", "sph_neighbour_list_static", "sph_sensor_pressure",
             "sph_sensor_adjoint", "sph_front_position", "sph_front_adjoint", "sph_adjoint_step",
-            "sph_error_string", "sph_destroy"]
+            "sph_fma_rate", "sph_error_string", "sph_destroy"]
 
 
 def _check(code, what):
@@ -318,6 +319,16 @@ def sph_neighbour_list_static(p: sph_params, n, pos, sorted_id, cell, cell_start
     _check(lib().sph_neighbour_list_static(C.byref(p), int(n), _ptr(pos), _ptr(sorted_id),
                                            _ptr(cell), _ptr(cell_start), stream),
            "sph_neighbour_list_static")
+
+
+def sph_fma_rate(precision, scratch, stream=None):
+    """Measured rate (FLOP/s, 2 per FMA) of float32 ("fp32") or float64
+    ("fp64") fused multiply-adds on the current device; scratch is a device
+    buffer of at least 8 bytes."""
+    out = C.c_double(0.0)
+    code = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    _check(lib().sph_fma_rate(code, _ptr(scratch), stream, C.byref(out)), "sph_fma_rate")
+    return out.value
 
 
 def sph_destroy(ctx):

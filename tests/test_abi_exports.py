@@ -88,3 +88,16 @@ def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(sph, "_lib", None)
     with pytest.raises(RuntimeError):
         sph.lib()
+
+
+def test_fma_rate_rejects_bad_arguments_before_any_cuda_call(libsph):
+    """sph_fma_rate checks its arguments on the host: no scratch, no output or
+    an unknown precision give SPH_ERR_INVALID_ARG without touching a GPU."""
+    import ctypes as C
+    from paper_1110_3711_gb300 import sph
+    L = sph.lib()
+    out = C.c_double(0.0)
+    assert L.sph_fma_rate(1, None, None, C.byref(out)) == -1
+    assert L.sph_fma_rate(1, C.c_void_p(16), None, None) == -1
+    assert L.sph_fma_rate(7, C.c_void_p(16), None, C.byref(out)) == -1
+    assert out.value == 0.0
