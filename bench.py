@@ -229,6 +229,12 @@ def run_form(torch, case, precision, steps, warmup, flush, world, clocks=False, 
                                stream=torch.cuda.current_stream())
     for _ in range(warmup):
         sim.step()
+    ckpt = None
+    if graph:
+        # the graph replays the same steps as the ordinary launches: the state
+        # after the warm-up is kept and restored before the graph is timed
+        ckpt = torch.empty(sim.checkpoint_bytes(), dtype=torch.uint8, device="cuda")
+        sim.save_state(ckpt)
     c0 = counts_now(sim)
     torch.cuda.synchronize()
     sampler = ClockSampler(local) if clocks else None
@@ -243,6 +249,7 @@ def run_form(torch, case, precision, steps, warmup, flush, world, clocks=False, 
     graph_res = None
     if graph:
         sim.run_graph(2)   # capture outside the timed region
+        sim.load_state(ckpt)
         torch.cuda.synchronize()
         barrier(world)
         g0 = sim.launches
@@ -497,12 +504,15 @@ def main():
                          "stage_ms": r_a["stage_ms"],
                          "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
         if args.fp64_steps > 0:
-            s_a, r_a = run_form(torch, fine, "fp64", args.fp64_steps, 3, flush, world)
-            del s_a
             abl["fp64"] = {"steps_per_s": r64["steps_per_s"], "pi_ms": r64["pi_ms"],
                            "candidates_per_step": r64["counts"][0] + r64["counts"][2]}
-            abl["fp64_hcells"] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
-                                  "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
+            for name, kname, cs in (("fp64_thread", "thread", case),
+                                    ("fp64_hcells", "warp", fine)):
+                s_a, r_a = run_form(torch, cs, "fp64", args.fp64_steps, 3, flush, world,
+                                    pi_kernel=kname)
+                del s_a
+                abl[name] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
+                             "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
         extra["pi_kernel_ablation"] = abl
     if not args.no_5m and args.workload != "dam5m":
         case5 = dam_break(WORKLOADS["dam5m"]["dp"])
@@ -539,7 +549,8 @@ def main():
         "interactions_per_s": r32["interactions_per_s"] * sps / r32["steps_per_s"],
         "timing": ("steps replayed from the library's CUDA graph (sph_run_graph, two steps per "
                    "replay, CUDA events around each replay); stage_ms and the PI roofline from a "
-                   "run of ordinary launches with events around each stage"),
+                   "run of ordinary launches with events around each stage over the same steps "
+                   "(state after the warm-up restored between the two runs)"),
         "plain_launches": {"steps_per_s": r32["steps_per_s"], "ms_per_step": r32["ms_per_step"]},
         "stage_ms": r32["stage_ms"],
         "fp64": (None if r64 is None else

@@ -53,7 +53,7 @@ extern "C" {
 #define SPH_FP32_SPLIT 1  /* PI in float32 on cell-relative float32 offsets; float64
                              position accumulation and time-step reduction */
 
-/* PI kernel designs of the split form (same arithmetic, different mapping) */
+/* PI kernel designs (same arithmetic, different mapping; see pi_kernel below) */
 #define SPH_PI_WARP              0  /* one warp per cell: lockstep candidate tests in
                                        shared memory, per-lane hit walks (default) */
 #define SPH_PI_THREAD            1  /* the paper's design: one thread per particle, 27
@@ -108,8 +108,11 @@ typedef struct sph_params {
     double fixed_dt;      /* > 0: constant time step; <= 0: variable */
     int64_t clamp_boundary_rho; /* 1: boundary density never drops below rho0 */
     int32_t precision;    /* SPH_FP64 or SPH_FP32_SPLIT */
-    int32_t pi_kernel;    /* SPH_PI_* (SPH_FP32_SPLIT only; SPH_FP64 always uses one
-                             thread per particle) */
+    int32_t pi_kernel;    /* SPH_PI_*.  SPH_FP64: SPH_PI_WARP (default: the warp-per-item
+                             kernel with float32 lockstep tests and float64 pairs when
+                             cell_size >= 2h, one thread per particle for finer cells)
+                             or SPH_PI_THREAD (one thread per particle); the other
+                             designs give SPH_ERR_INVALID_ARG */
     /* Tensile correction (Monaghan 2000; the "tensil" term of Table 3), off when
      * both coefficients are 0: the momentum term P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab
      * gains R_ab (W(r)/W(dp))^n with R_ab = tensile_pos (P_a/rho_a^2 + P_b/rho_b^2)

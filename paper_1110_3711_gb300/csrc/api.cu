@@ -51,6 +51,9 @@ int validate(const sph_params *p, int64_t nf, int64_t nb, int dims[3], uint32_t 
     // searched by the float64 kernels and the thread-per-particle kernel only
     if (cell_reach(*p) > 1 && p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_THREAD)
         return SPH_ERR_INVALID_ARG;
+    // float64: the warp-per-item kernel or one thread per particle
+    if (p->precision == SPH_FP64 && p->pi_kernel != SPH_PI_WARP && p->pi_kernel != SPH_PI_THREAD)
+        return SPH_ERR_INVALID_ARG;
     const bool tensile = p->tensile_eps != 0.0 || p->tensile_pos != 0.0;
     if (tensile && (p->tensile_n < 1 || p->tensile_n > 16 || !(p->dp > 0) ||
                     (p->precision == SPH_FP32_SPLIT && p->pi_kernel != SPH_PI_WARP)))
@@ -505,6 +508,8 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b, const double *pos,
     if (!rc) rc = fill_origins(ctx);
     if (!rc && ctx->precision == SPH_FP32_SPLIT)
         rc = p->pi_kernel == SPH_PI_WARP_SYM ? pi32_sym_setup(ctx) : pi32_setup(ctx);
+    else if (!rc)
+        rc = pi64_setup(ctx);
     if (!rc) rc = load_state(ctx, pos, vel, rho, nullptr, nullptr);
     if (rc) {
         free(ctx);

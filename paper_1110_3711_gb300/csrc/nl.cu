@@ -461,7 +461,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
         for (int k = b; k < e; ++k) r += id_q[k] < myid ? 1 : 0;
         p = b + r;
         // a PI work item starts at every 32nd particle of a cell
-        if (SPLIT && c < P.ncells) item = (r & 31) == 0;
+        if (c < P.ncells) item = (r & 31) == 0;
         dx[p] = x; dy[p] = y; dz[p] = z;
         dvx[p] = vx; dvy[p] = vy; dvz[p] = vz;
         dvmx[p] = vmx; dvmy[p] = vmy; dvmz[p] = vmz;
@@ -512,7 +512,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
             bvelr[j] = vv;
         }
     }
-    if (SPLIT) {
+    {
         // warp-aggregated append of the work items (their order does not matter)
         unsigned ball = __ballot_sync(0xffffffffu, item);
         if (ball) {
@@ -670,10 +670,8 @@ static int nl_boundary_t(sph_ctx *ctx)
     int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.bstart, (int64_t)ctx->ncells + 2,
                                 w.scan_part, st);
     if (rc) return rc;
-    if (SPLIT) {
-        rc = boundary_items_launch(ctx);
-        if (rc) return rc;
-    }
+    rc = boundary_items_launch(ctx);
+    if (rc) return rc;
     return check_cuda(cudaGetLastError());
 }
 

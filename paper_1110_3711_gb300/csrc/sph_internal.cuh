@@ -127,7 +127,7 @@ struct sph_ctx {
     bool nl_valid, pi_valid;
     long long launches;
     int device;
-    int pi_grid_f;              // persistent grid size of the FP32 warp PI kernels
+    int pi_grid_f;              // persistent grid size of the warp PI kernels
     bool branges_ready;         // boundary x-run table built for the current boundary list
     bool boundary_built;        // the boundary list exists (built at least once)
     // sph_run_graph: executable graphs of two consecutive steps, one per value
@@ -167,6 +167,7 @@ int pi32_setup(sph_ctx *ctx);
 int fill_origins(sph_ctx *ctx);
 int pi32_sym_launch(sph_ctx *ctx);
 int pi32_sym_setup(sph_ctx *ctx);
+int pi64_setup(sph_ctx *ctx);
 int boundary_items_launch(sph_ctx *ctx);
 int count_work_launch(sph_ctx *ctx);
 constexpr int kCtrWords = 4;     // work-item counters after the cell counts

@@ -79,6 +79,15 @@ def test_error_strings_and_workspace_on_cpu(libsph):
     q.cell_size = 0.99 * c.params.h
     with pytest.raises(sph.SphError):
         sph.sph_workspace_bytes(q, c.n_f, c.n_b)
+    # float64: the warp-per-item design or one thread per particle
+    for kern, ok in (("warp", True), ("thread", True), ("thread_fastcells", False),
+                     ("warp_sym", False)):
+        q = sph.make_params(c.params, "fp64", kern)
+        if ok:
+            assert sph.sph_workspace_bytes(q, c.n_f, c.n_b) > ws
+        else:
+            with pytest.raises(sph.SphError):
+                sph.sph_workspace_bytes(q, c.n_f, c.n_b)
 
 
 def test_no_cpu_fallback_without_library(monkeypatch, tmp_path):

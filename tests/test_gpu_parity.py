@@ -152,13 +152,18 @@ def _random_state(case, seed=0):
     return vel, rho
 
 
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread"])
 @pytest.mark.parametrize("case_fn", [lambda: dam_break(0.02),
-                                     lambda: random_cloud(3000, box=0.1, dp=0.008, n_b=700, seed=5)])
-def test_pi_fp64_matches_oracle(torch_mod, O, case_fn):
+                                     lambda: random_cloud(3000, box=0.1, dp=0.008, n_b=700, seed=5),
+                                     lambda: random_cloud(4000, box=0.1, dp=0.01, n_b=600, seed=21)])
+def test_pi_fp64_matches_oracle(torch_mod, O, case_fn, pi_kernel):
+    """float64 PI, both float64 designs; the last cloud has cells of up to
+    about 110 particles (several work items per cell, several staging passes
+    per item in the warp design)."""
     c = case_fn()
     vel, rho = _random_state(c, 1)
     c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho})
-    sim = make_sim(c2, "fp64")
+    sim = make_sim(c2, "fp64", pi_kernel=pi_kernel)
     sim.neighbour_list()
     sim.interact()
     ace, ar, mx = sim.forces()
@@ -229,6 +234,32 @@ def test_pi_fp32_with_particles_outside_the_grid(torch_mod, O, pi_kernel):
     keep = np.setdiff1d(np.arange(c.n_f), out)
     assert np.abs(ace[keep] - oace[keep]).max() / (9.81 + np.abs(oace).max()) < 2e-5
     assert np.abs(ar - oar)[np.r_[keep, np.arange(c.n_f, c.n)]].max() / np.abs(oar).max() < 2e-5
+    from paper_1110_3711_gb300.sph import FLAG_OUT_OF_GRID
+    assert sim.status(clear=True) & FLAG_OUT_OF_GRID
+
+
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread"])
+def test_pi_fp64_with_particles_outside_the_grid(torch_mod, O, pi_kernel):
+    """float64 PI with fluid particles outside the grid: their outputs are 0,
+    every other particle's match the oracle's to 1e-12."""
+    c = dam_break(0.02)
+    vel, rho = _random_state(c, 3)
+    pos = c.pos.copy()
+    out = [5, 77, 4000]
+    pos[5] = [-5.0, 0.1, 0.1]
+    pos[77] = [0.2, 0.2, 50.0]
+    pos[4000] = [0.3, -1.0, 0.05]
+    c2 = type(c)(**{**c.__dict__, "pos": pos, "vel": vel, "rho": rho})
+    sim = make_sim(c2, "fp64", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, _ = sim.forces()
+    oace, oar, _, _, nout = O.interact(c.params, c.n_f, c.n_b, pos, vel, rho)
+    assert nout == len(out)
+    keep = np.setdiff1d(np.arange(c.n_f), out)
+    assert np.abs(ace[keep] - oace[keep]).max() <= 1e-12 * np.abs(oace).max()
+    assert np.abs(ar - oar)[np.r_[keep, np.arange(c.n_f, c.n)]].max() <= 1e-12 * np.abs(oar).max()
+    assert np.all(ace[out] == 0.0) and np.all(ar[out] == 0.0)
     from paper_1110_3711_gb300.sph import FLAG_OUT_OF_GRID
     assert sim.status(clear=True) & FLAG_OUT_OF_GRID
 
@@ -424,7 +455,7 @@ def test_graph_replay_equals_plain_steps(torch_mod, precision, steps):
 
 
 @pytest.mark.parametrize("variant", ["thread", "thread_fastcells", "thread_hcells", "fp64_hcells",
-                                     "warp_tensile"])
+                                     "fp64_thread", "warp_tensile"])
 def test_graph_replay_other_designs(torch_mod, variant):
     """The captured graph replays every deterministic design bit for bit."""
     import dataclasses
@@ -435,6 +466,8 @@ def test_graph_replay_other_designs(torch_mod, variant):
         p = dataclasses.replace(c.params, cell_size=c.params.h)
         c = type(c)(**{**c.__dict__, "params": p})
         prec, kern = ("fp64", "warp") if variant.startswith("fp64") else ("fp32", "thread")
+    if variant == "fp64_thread":
+        prec, kern = "fp64", "thread"
     if variant == "warp_tensile":
         p = dataclasses.replace(c.params, tensile_eps=0.2, tensile_pos=0.01)
         c = type(c)(**{**c.__dict__, "params": p})
