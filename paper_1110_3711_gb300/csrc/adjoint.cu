@@ -16,8 +16,11 @@
 // depends on r_ab, v_ab, rho_a, rho_b and alpha; because the neighbour
 // relation is symmetric, every particle collects the derivatives of the
 // pairs it receives (a = self) and of the pairs it sources (b = self) by
-// walking its own 27 cells once: a gather, no atomics, deterministic.
-// dJ/dalpha is summed per block and the block sums are added in order.
+// walking its own 27 cells once: a gather, no atomics, deterministic.  With
+// cells of edge 2h the walk runs on the warp work items of the float64 PI
+// (warp_items.cuh) and dJ/dalpha is summed per item; with finer cells one
+// thread walks per particle and dJ/dalpha is summed per block.  The partial
+// sums are added in a fixed order.
 //
 // Arrays exchanged with the caller (lam, lam_next) are float64 in
 // persistent-id order with the layout of sph_get_state:
@@ -27,6 +30,7 @@
 #include <stdint.h>
 
 #include "sph_internal.cuh"
+#include "warp_items.cuh"
 
 namespace sph {
 
@@ -429,11 +433,142 @@ __global__ void k_adj_out(int nf, int nb, size_t N, const uint32_t *__restrict__
     lam[10 * N + k] = lam_s[10 * N + i];
 }
 
-__global__ void k_adj_alpha(const double *__restrict__ part, int n, double *dalpha)
+// ---- adjoint PI on the warp work items (cells of edge 2h or more) -------------
+//
+// The candidate search of the float64 PI kernel (warp_items.cuh): every lane
+// walks the hits of its own target and sums pair_adj (fluid targets, F-F and
+// F-B with their B-F counterparts) or pair_adj_rho_b (boundary targets) in
+// the item's fixed order.  dJ/dalpha of an item is summed over its lanes in a
+// fixed order and stored at its first target, so the total does not depend on
+// the order the items are processed in.
+
+constexpr int kAdjWarps = 4;
+
+__device__ __forceinline__ void adj_fluid_item(
+    const DevParams &P, witems::Smem &S, int lane, uint32_t it, int nf, size_t N,
+    const uint32_t *__restrict__ items, const double4_32a *__restrict__ posp,
+    const double4_32a *__restrict__ velr, const float4 *__restrict__ posf,
+    const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
+    const double4_32a *__restrict__ bposp, const double4_32a *__restrict__ bvelr,
+    const float4 *__restrict__ bposf, const int32_t *__restrict__ bstart,
+    const double *__restrict__ gF, const double *__restrict__ gD, double *__restrict__ lam_s,
+    double *__restrict__ part)
 {
+    const witems::Item I = witems::item_of<true>(P, items, it, cell, fstart, lane);
+    const int i = I.i;
+    const double4_32a pa = posp[i], va = velr[i];
+    const PartTerms ta = part_terms(P, va.w, pa.w);
+    const double gFx = gF[3 * (size_t)i], gFy = gF[3 * (size_t)i + 1],
+                 gFz = gF[3 * (size_t)i + 2], gDa = gD[i];
+    const witems::Frame Fr = witems::frame_of<true>(P, I, posf[i], cell);
+    const double s2 = 4.0 * P.h * P.h;
+    SelfAdj l = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+    witems::for_each_hit<true>(P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
+                               [&](int j, bool blist) {
+        if (!blist) {
+            if (j == i) return;
+            const double4_32a pb = posp[j];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+            const double4_32a vb = velr[j];
+            pair_adj<true>(P, rx, ry, rz, va.x - vb.x, va.y - vb.y, va.z - vb.z, ta, vb.w, pb.w,
+                           sound_of(P, vb.w), gFx, gFy, gFz, gF[3 * (size_t)j],
+                           gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gDa + gD[j], l);
+        } else {
+            const double4_32a pb = bposp[j];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+            const double rho_b = bvelr[j].w;
+            pair_adj<false>(P, rx, ry, rz, va.x, va.y, va.z, ta, rho_b, pb.w, sound_of(P, rho_b),
+                            gFx, gFy, gFz, 0.0, 0.0, 0.0, gDa + gD[(size_t)nf + j], l);
+        }
+    });
+    if (I.active) {
+        double *ox = lam_s + 3 * (size_t)i, *ov = lam_s + 3 * N + 3 * (size_t)i;
+        ox[0] += l.rx; ox[1] += l.ry; ox[2] += l.rz;
+        ov[0] += l.vx; ov[1] += l.vy; ov[2] += l.vz;
+        lam_s[6 * N + i] += l.rho;
+    }
+    double a = I.active ? l.alpha : 0.0;
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) part[I.i0] = a;
+}
+
+__device__ __forceinline__ void adj_boundary_item(
+    const DevParams &P, witems::Smem &S, int lane, uint32_t it, int nf, size_t N,
+    const uint32_t *__restrict__ items, const double4_32a *__restrict__ bposp,
+    const double4_32a *__restrict__ bvelr, const float4 *__restrict__ bposf,
+    const uint32_t *__restrict__ bcell, const int32_t *__restrict__ bstart,
+    const double4_32a *__restrict__ posp, const double4_32a *__restrict__ velr,
+    const float4 *__restrict__ posf, const uint32_t *__restrict__ cell,
+    const int32_t *__restrict__ fstart, const double *__restrict__ gF,
+    double *__restrict__ lam_s)
+{
+    const witems::Item I = witems::item_of<false>(P, items, it, bcell, bstart, lane);
+    const int j = I.i;
+    const double4_32a pb = bposp[j], vb = bvelr[j];
+    const PartTerms tb = part_terms(P, vb.w, pb.w);
+    const witems::Frame Fr = witems::frame_of<false>(P, I, bposf[j], bcell);
+    const double s2 = 4.0 * P.h * P.h;
+    double lr = 0.0;
+    witems::for_each_hit<false>(P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
+                                [&](int i, bool) {
+        const double4_32a pa = posp[i];
+        const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+        if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+        const double4_32a va = velr[i];
+        lr += pair_adj_rho_b(P, rx, ry, rz, va.x, va.y, va.z, tb, va.w, sound_of(P, va.w),
+                             gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2]);
+    });
+    if (I.active) lam_s[6 * N + (size_t)nf + j] += lr;
+}
+
+// One queue: the fluid items, then the boundary items, over a persistent grid.
+__global__ void __launch_bounds__(kAdjWarps * 32)
+k_adj_pi_w(int nf, size_t N, DevParams P, const uint32_t *__restrict__ items_f,
+           const uint32_t *__restrict__ items_b, const uint32_t *__restrict__ ctr, int use_b,
+           uint32_t *__restrict__ next_p, const double4_32a *__restrict__ posp,
+           const double4_32a *__restrict__ velr, const float4 *__restrict__ posf,
+           const uint32_t *__restrict__ cell, const int32_t *__restrict__ fstart,
+           const double4_32a *__restrict__ bposp, const double4_32a *__restrict__ bvelr,
+           const float4 *__restrict__ bposf, const uint32_t *__restrict__ bcell,
+           const int32_t *__restrict__ bstart, const double *__restrict__ gF,
+           const double *__restrict__ gD, double *__restrict__ lam_s, double *__restrict__ part)
+{
+    __shared__ witems::Smem smem[kAdjWarps];
+    const int lane = threadIdx.x & 31;
+    witems::Smem &S = smem[threadIdx.x >> 5];
+    const uint32_t nfi = ctr[0];
+    const uint32_t n_items = nfi + (use_b ? ctr[3] : 0u);
+    for (;;) {
+        uint32_t it = 0;
+        if (lane == 0) it = atomicAdd(next_p, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if (it >= n_items) break;
+        if (it < nfi)
+            adj_fluid_item(P, S, lane, it, nf, N, items_f, posp, velr, posf, cell, fstart, bposp,
+                           bvelr, bposf, bstart, gF, gD, lam_s, part);
+        else
+            adj_boundary_item(P, S, lane, it - nfi, nf, N, items_b, bposp, bvelr, bposf, bcell,
+                              bstart, posp, velr, posf, cell, fstart, gF, lam_s);
+    }
+}
+
+// dJ/dalpha += sum of part[0 .. n): one block, each thread sums a fixed strided
+// subset in order, then a fixed-order tree: deterministic.
+__global__ void __launch_bounds__(1024) k_adj_alpha(const double *__restrict__ part, int n,
+                                                    double *dalpha)
+{
+    __shared__ double t[1024];
     double s = 0.0;
-    for (int k = 0; k < n; ++k) s += part[k];
-    *dalpha += s;
+    for (int k = threadIdx.x; k < n; k += 1024) s += part[k];
+    t[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 512; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) t[threadIdx.x] += t[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *dalpha += t[0];
 }
 
 // ---- sensor objective ---------------------------------------------------------
@@ -662,6 +797,20 @@ extern "C" int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n
     return check_cuda(cudaGetLastError());
 }
 
+// Persistent grid of the work-item adjoint kernel: one resident set of CTAs.
+int sph::adjoint_setup(sph_ctx *ctx)
+{
+    int dev = 0, sms = 0, nblk = 0;
+    if (check_cuda(cudaGetDevice(&dev))) return SPH_ERR_CUDA;
+    if (check_cuda(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)))
+        return SPH_ERR_CUDA;
+    if (check_cuda(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nblk, k_adj_pi_w,
+                                                                kAdjWarps * 32, 0)))
+        return SPH_ERR_CUDA;
+    ctx->adj_grid = sms * (nblk > 0 ? nblk : 1);
+    return SPH_OK;
+}
+
 extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *dalpha)
 {
     if (!ctx || !lam_next || !lam || !dalpha || lam_next == lam) return SPH_ERR_INVALID_ARG;
@@ -685,20 +834,34 @@ extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *la
         SPH_LAUNCH(ctx, k_adj_su_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
                    w.bstart, w.bid, (const double *)w.brho, (const double *)w.brhom,
                    (const double *)w.bar, lam_next, w.adj_lam, w.adj_gD, w.sc);
-    if (nf > 0)
-        SPH_LAUNCH(ctx, k_adj_pi_fluid, blocks_f, T, 0, st, nf, N, ctx->dp,
-                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
-                   (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
-                   w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part, w.posf, w.bposf);
-    if (nb > 0 && nf > 0)
-        SPH_LAUNCH(ctx, k_adj_pi_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
-                   (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
-                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, w.adj_gF,
-                   w.adj_gD, w.adj_lam, w.posf, w.bposf);
+    int nparts = blocks_f;
+    if (ctx->dp.reach == 1 && nf > 0) {
+        // work items of this step's NL (cells of edge 2h or more)
+        if (check_cuda(cudaMemsetAsync(w.adj_part, 0, sizeof(double) * (size_t)nf, st)))
+            return SPH_ERR_CUDA;
+        if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, sizeof(uint32_t), st))) return SPH_ERR_CUDA;
+        SPH_LAUNCH(ctx, k_adj_pi_w, ctx->adj_grid, kAdjWarps * 32, 0, st, nf, N, ctx->dp,
+                   w.items_f, w.items_b, w.ctr, nb > 0 ? 1 : 0, &w.ctr[1],
+                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.posf, w.cell,
+                   w.fstart, (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bposf,
+                   w.bcell, w.bstart, w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part);
+        nparts = nf;
+    } else {
+        if (nf > 0)
+            SPH_LAUNCH(ctx, k_adj_pi_fluid, blocks_f, T, 0, st, nf, N, ctx->dp,
+                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
+                       (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
+                       w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part, w.posf, w.bposf);
+        if (nb > 0 && nf > 0)
+            SPH_LAUNCH(ctx, k_adj_pi_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
+                       (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell,
+                       w.bstart, (const double4_32a *)w.posp, (const double4_32a *)w.velr,
+                       w.fstart, w.adj_gF, w.adj_gD, w.adj_lam, w.posf, w.bposf);
+    }
     if (N > 0)
         SPH_LAUNCH(ctx, k_adj_out, (unsigned)((N + T - 1) / T), T, 0, st, nf, nb, N, w.id[c],
                    w.bid, w.adj_lam, lam);
-    if (nf > 0) SPH_LAUNCH(ctx, k_adj_alpha, 1, 1, 0, st, w.adj_part, blocks_f, dalpha);
+    if (nf > 0) SPH_LAUNCH(ctx, k_adj_alpha, 1, 1024, 0, st, w.adj_part, nparts, dalpha);
     return check_cuda(cudaGetLastError());
 }
 

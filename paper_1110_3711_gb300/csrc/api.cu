@@ -235,7 +235,7 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
         W.adj_gF = b.take<double>(3 * (size_t)nf + 1);
         W.adj_gD = b.take<double>((size_t)(nf + nb) + 1);
         W.adj_lam = b.take<double>((size_t)11 * (size_t)(nf + nb) + 1);
-        W.adj_part = b.take<double>((size_t)(nf / 128 + 2));
+        W.adj_part = b.take<double>((size_t)nf + 2);   // dJ/dalpha per work item (first target)
     }
     W.sens_p = b.take<double>(kMaxSensors);
     W.sens_den = b.take<double>(kMaxSensors);
@@ -510,6 +510,7 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b, const double *pos,
         rc = p->pi_kernel == SPH_PI_WARP_SYM ? pi32_sym_setup(ctx) : pi32_setup(ctx);
     else if (!rc)
         rc = pi64_setup(ctx);
+    if (!rc && ctx->precision == SPH_FP64) rc = adjoint_setup(ctx);
     if (!rc) rc = load_state(ctx, pos, vel, rho, nullptr, nullptr);
     if (rc) {
         free(ctx);

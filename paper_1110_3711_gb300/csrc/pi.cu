@@ -27,6 +27,7 @@
 #include <stdint.h>
 
 #include "sph_internal.cuh"
+#include "warp_items.cuh"
 
 namespace sph {
 
@@ -278,37 +279,20 @@ __global__ void k_count_work(int nf, int nb, DevParams P, const double *__restri
 
 // ------------------------------------------------- FP64, warp per work item --
 //
-// The work items of the FP32 warp kernel (up to 32 fluid targets of one cell;
-// packed boundary items of consecutive cells of one x row) with float64
-// pairs.  The warp stages the float32 cell-relative offsets of its
-// candidates (units of h, shifted into the frame of the item's first cell)
-// and tests them against all its targets in lockstep, in float32, against
-// 4 (1 + 1e-4) (units of h^2): far above the float32 error of the offsets
-// and of the test (below 1e-5 of 4), so every pair of the float64 test is a
-// hit.  Each lane then walks its own hits with the float64 test and the
-// float64 pair of pair64, so the float64 unit works on near neighbours with
-// the lanes of the warp busy together (the thread-per-target kernel above
-// runs its pair branch with the lanes whose candidate passed).  Cells of edge
-// 2h or more only (9 x-runs per list).
+// The work items of the FP32 warp kernel with float64 pairs (warp_items.cuh):
+// float32 lockstep tests of the staged cell-relative offsets, then each lane
+// walks its own hits with the float64 test and the float64 pair of pair64, so
+// the float64 unit works on near neighbours with the lanes of the warp busy
+// together (the thread-per-target kernel above runs its pair branch with the
+// lanes whose candidate passed).  Cells of edge 2h or more only.
 
 namespace {
 
-constexpr int W64_CAP = 256;
-constexpr int W64_NCH = W64_CAP / 32;
 constexpr int W64_WARPS = 4;
-constexpr int W64_NRUN = 18;
-
-struct Warp64Smem {
-    float4 A[W64_CAP];         // shifted offset {x, y, z} (units of h) and |x|^2
-    uint32_t J[W64_CAP];       // candidate index, bit 31 set for the boundary list
-    uint32_t M[W64_NCH][32];   // hit bits of lane l for chunk q
-    int4 run[W64_NRUN];        // {inclusive end slot, first index, b1, b2} as in pi32.cu
-    int code[W64_NRUN];        // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
-};
 
 template <bool MOMENTUM>
 __device__ __forceinline__ void pi64_item(
-    const DevParams &P, Warp64Smem &S, int lane, uint32_t it, const uint32_t *__restrict__ items,
+    const DevParams &P, witems::Smem &S, int lane, uint32_t it, const uint32_t *__restrict__ items,
     const double4_32a *__restrict__ tposp, const double4_32a *__restrict__ tvelr,
     const float4 *__restrict__ tposf, const uint32_t *__restrict__ tcell,
     const int32_t *__restrict__ tstart, const double4_32a *__restrict__ fposp,
@@ -319,140 +303,23 @@ __device__ __forceinline__ void pi64_item(
     double4_32a *__restrict__ acc, double *__restrict__ bar, double &f2max, double &vismax,
     bool &bad)
 {
-    const int nlists = MOMENTUM ? 2 : 1;
-    int i0, nt;
-    if (MOMENTUM) {
-        i0 = (int)items[it];
-        nt = min(32, tstart[tcell[i0] + 1] - i0);
-    } else {
-        i0 = (int)items[2 * it];
-        nt = (int)items[2 * it + 1];
-    }
-    const uint32_t c = tcell[i0];
-    const bool active = lane < nt;
-    const int i = i0 + (active ? lane : 0);
+    const witems::Item I = witems::item_of<MOMENTUM>(P, items, it, tcell, tstart, lane);
+    const int i = I.i;
     const double4_32a pa = tposp[i], va = tvelr[i];
-    const float4 fa = tposf[i];
-    int cx, cy, cz;
-    cell_xyz(P, c, &cx, &cy, &cz);
-    const int cx1 = MOMENTUM ? cx : cx + (int)(tcell[i0 + nt - 1] - c);
-    const float tshift = MOMENTUM ? 0.0f : (float)(int)(tcell[i] - c) * P.s_hf;
-    const float xa = fmaf(fa.x, P.invhf, tshift), ya = fa.y * P.invhf, za = fa.z * P.invhf;
-    const float m2x = -2.0f * xa, m2y = -2.0f * ya, m2z = -2.0f * za;
-    const float thr = active ? 4.0004f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
+    const witems::Frame Fr = witems::frame_of<MOMENTUM>(P, I, tposf[i], tcell);
     const double ca = MOMENTUM ? sound64(P, va.w) : 0.0;
     const double s2 = 4.0 * P.h * P.h;
-
-    // ---- run table: lane r describes run r
-    int K;
-    {
-        const int r = lane;
-        int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
-        if (r < 9 * nlists) {
-            const int list = r / 9, q = r % 9;
-            const int dz = q / 3 - 1, dy = q % 3 - 1;
-            const int y = cy + dy, z = cz + dz;
-            code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
-            if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
-                const int32_t *st = list ? bstart : fstart;
-                const int row = P.nx * (y + P.ny * z);
-                const int x0 = max(cx - 1, 0), x1 = min(cx1 + 1, P.nx - 1);
-                j0 = st[row + x0];
-                L = st[row + x1 + 1] - j0;
-                if (MOMENTUM) {
-                    b1 = st[row + cx];
-                    b2 = st[row + cx + 1];
-                } else {
-                    b1 = row + cx;
-                }
-            }
-        }
-        int pe = L;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, pe, o);
-            if (lane >= o) pe += t;
-        }
-        if (r < W64_NRUN) {
-            S.run[r] = make_int4(pe, j0, b1, b2);
-            S.code[r] = code;
-        }
-        K = __shfl_sync(0xffffffffu, pe, W64_NRUN - 1);
-    }
-    __syncwarp();
-
     Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
-    const int npass = (K + W64_CAP - 1) / W64_CAP;
-    for (int pass = 0; pass < npass; ++pass) {
-        const int np = (K - pass + npass - 1) / npass;
-        const int nch = (np + 31) >> 5;
-        int r = 0;
-        for (int m = 0; m < nch; ++m) {
-            const int ls = lane + 32 * m;
-            const int sidx = ls < np ? pass + npass * ls : K;
-            float4 a;
-            uint32_t jj = 0;
-            if (sidx < K) {
-                while (sidx >= S.run[r].x) ++r;
-                const int4 ri = S.run[r];
-                const int prev = r ? S.run[r - 1].x : 0;
-                const int j = ri.y + (sidx - prev);
-                const int cd = S.code[r];
-                const float sx = MOMENTUM ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
-                                          : (float)((int)fcell[j] - ri.z) * P.s_hf;
-                const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-                const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-                const bool blist = MOMENTUM && (cd & 1);
-                const float4 f = blist ? bposf[j] : fposf[j];
-                a.x = fmaf(f.x, P.invhf, sx);
-                a.y = fmaf(f.y, P.invhf, sy);
-                a.z = fmaf(f.z, P.invhf, sz);
-                a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
-            } else {
-                a = make_float4(0.f, 0.f, 0.f, INFINITY);
-            }
-            S.A[ls] = a;
-            S.J[ls] = jj;
-        }
-        __syncwarp();
-        for (int q = 0; q < nch; ++q) {
-            uint32_t lo = 0u, hi = 0u;
-#pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float4 a = S.A[q * 32 + k];
-                const float4 b = S.A[q * 32 + 16 + k];
-                const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - thr;
-                const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - thr;
-                lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-                hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
-            }
-            S.M[q][lane] = __brev((lo << 16) | hi);
-        }
-        int q = 0;
-        uint32_t m = S.M[0][lane];
-        for (;;) {
-            while (m == 0u && q + 1 < nch) {
-                ++q;
-                m = S.M[q][lane];
-            }
-            if (m == 0u) break;
-            const int ls = q * 32 + __ffs(m) - 1;
-            m &= m - 1u;
-            const uint32_t jj = S.J[ls];
-            const bool blist = MOMENTUM && (jj >> 31);
-            const int j = (int)(jj & 0x7fffffffu);
-            if (MOMENTUM && !blist && j == i) continue;   // the target itself
-            const double4_32a pb = blist ? bposp[j] : fposp[j];
-            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
-            const double r2 = rx * rx + ry * ry + rz * rz;
-            if (r2 < s2)
-                pair64<MOMENTUM>(P, pa, va, ca, pb, blist ? bvelr[j] : fvelr[j], rx, ry, rz, r2, o);
-        }
-        __syncwarp();
-    }
-
-    if (active) {
+    witems::for_each_hit<MOMENTUM>(P, S, lane, I, Fr, fstart, fposf, bstart, bposf, fcell,
+                                   [&](int j, bool blist) {
+        if (MOMENTUM && !blist && j == i) return;   // the target itself
+        const double4_32a pb = blist ? bposp[j] : fposp[j];
+        const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+        const double r2 = rx * rx + ry * ry + rz * rz;
+        if (r2 < s2)
+            pair64<MOMENTUM>(P, pa, va, ca, pb, blist ? bvelr[j] : fvelr[j], rx, ry, rz, r2, o);
+    });
+    if (I.active) {
         if (MOMENTUM) {
             const double ax = P.mass * o.ax + P.g[0];
             const double ay = P.mass * o.ay + P.g[1];
@@ -483,10 +350,10 @@ k_pi64w(DevParams P, int nf, int nb, const uint32_t *__restrict__ items_f,
         const uint32_t *__restrict__ bcell, const int32_t *__restrict__ bstart,
         double4_32a *__restrict__ acc, double *__restrict__ bar, Scalars *sc)
 {
-    __shared__ Warp64Smem smem[W64_WARPS];
+    __shared__ witems::Smem smem[W64_WARPS];
     __shared__ double red[32];
     const int lane = threadIdx.x & 31;
-    Warp64Smem &S = smem[threadIdx.x >> 5];
+    witems::Smem &S = smem[threadIdx.x >> 5];
     const uint32_t nfi = ctr[0];
     const uint32_t n_items = nfi + (use_b ? ctr[3] : 0u);
     double f2max = 0.0, vismax = 0.0;

@@ -100,7 +100,8 @@ struct Workspace {
     uint32_t *radix_hist;     // [256 * tiles]
     uint32_t *scan_part;      // scan partials
     // adjoint scratch (SPH_FP64 contexts): cotangents of F and D, the adjoint
-    // in sorted order (11 doubles per particle), per-block dJ/dalpha
+    // in sorted order (11 doubles per particle), dJ/dalpha partial sums (per
+    // work item at its first target, or per block)
     double *adj_gF, *adj_gD, *adj_lam, *adj_part;
     double *sens_p, *sens_den;  // sensor pressures and Shepard denominators
     double *front;              // front position: max x and the sum of exp((x - max) / tau)
@@ -128,6 +129,7 @@ struct sph_ctx {
     long long launches;
     int device;
     int pi_grid_f;              // persistent grid size of the warp PI kernels
+    int adj_grid;               // persistent grid size of the work-item adjoint kernel
     bool branges_ready;         // boundary x-run table built for the current boundary list
     bool boundary_built;        // the boundary list exists (built at least once)
     // sph_run_graph: executable graphs of two consecutive steps, one per value
@@ -168,6 +170,7 @@ int fill_origins(sph_ctx *ctx);
 int pi32_sym_launch(sph_ctx *ctx);
 int pi32_sym_setup(sph_ctx *ctx);
 int pi64_setup(sph_ctx *ctx);
+int adjoint_setup(sph_ctx *ctx);   // adjoint.cu
 int boundary_items_launch(sph_ctx *ctx);
 int count_work_launch(sph_ctx *ctx);
 constexpr int kCtrWords = 4;     // work-item counters after the cell counts

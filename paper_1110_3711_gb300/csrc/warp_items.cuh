@@ -1,0 +1,212 @@
+// Warp-per-work-item candidate search shared by the float64 kernels (PI and
+// its adjoint).
+//
+// A work item is up to 32 fluid targets of one cell (items_f, one entry per
+// first target) or up to 32 boundary targets of consecutive cells of one x
+// row (items_b, {first, count} pairs).  For an item the warp
+//   1. builds the table of its x-runs (Section 4.4, Fig. 10): for every
+//      (dy, dz) of the 9 neighbour rows, cells x-1 .. x+1 (of the item's first
+//      and last cell) are one index range of the fluid list, and for fluid
+//      targets of the boundary list too;
+//   2. stages the candidates of those runs in shared memory as their float32
+//      cell-relative offsets shifted into the frame of the item's first cell,
+//      in units of h, with |x|^2 beside them, and their indices;
+//   3. tests every candidate against every target in lockstep, in float32,
+//      against 4 (1 + 1e-4) (units of h^2): the float32 error of the offsets
+//      and of the test is below 1e-5 of 4, so every pair of the float64 test
+//      r^2 < 4h^2 is a hit (the float64 test then decides);
+//   4. lets every lane walk its own hits in staging order, calling the
+//      caller's hit function with the candidate's index and list.
+// Neighbourhoods of more than CAP candidates take several passes; pass p
+// stages candidates p, p + npass, ..., so that each pass holds about 1/npass
+// of every lane's neighbours.  The walk order depends only on the item, so
+// sums accumulated in it are deterministic.  Cells of edge 2h or more only.
+#pragma once
+
+#include "sph_internal.cuh"
+
+namespace sph {
+namespace witems {
+
+constexpr int CAP = 256;
+constexpr int NCH = CAP / 32;
+constexpr int NRUN = 18;   // 9 fluid + 9 boundary x-runs
+
+struct Smem {
+    float4 A[CAP];          // shifted offset {x, y, z} (units of h) and |x|^2
+    uint32_t J[CAP];        // candidate index, bit 31 set for the boundary list
+    uint32_t M[NCH][32];    // hit bits of lane l for chunk q
+    int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
+    int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
+};
+
+// The item's targets as one lane sees them.
+struct Item {
+    int i0, nt;             // first target, number of targets
+    int i;                  // this lane's target (i0 for lanes past nt)
+    bool active;            // lane < nt
+    uint32_t c;             // cell of the first target
+    int cx, cy, cz, cx1;    // its coordinates; cx1: x of the item's last cell
+};
+
+template <bool FLUID_TARGETS>
+__device__ __forceinline__ Item item_of(const DevParams &P, const uint32_t *__restrict__ items,
+                                        uint32_t it, const uint32_t *__restrict__ tcell,
+                                        const int32_t *__restrict__ tstart, int lane)
+{
+    Item I;
+    if (FLUID_TARGETS) {
+        I.i0 = (int)items[it];
+        I.nt = min(32, tstart[tcell[I.i0] + 1] - I.i0);
+    } else {
+        I.i0 = (int)items[2 * it];
+        I.nt = (int)items[2 * it + 1];
+    }
+    I.c = tcell[I.i0];
+    I.active = lane < I.nt;
+    I.i = I.i0 + (I.active ? lane : 0);
+    const uint32_t t = I.c / (uint32_t)P.nx;
+    I.cx = (int)(I.c - t * (uint32_t)P.nx);
+    I.cy = (int)(t % (uint32_t)P.ny);
+    I.cz = (int)(t / (uint32_t)P.ny);
+    I.cx1 = FLUID_TARGETS ? I.cx : I.cx + (int)(tcell[I.i0 + I.nt - 1] - I.c);
+    return I;
+}
+
+// Lane's target in the item's frame (units of h): x, y, z and the test
+// threshold 4 (1 + 1e-4) - |x|^2 (-inf for idle lanes).
+struct Frame {
+    float x, y, z, thr;
+};
+
+template <bool FLUID_TARGETS>
+__device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, const float4 &fa,
+                                          const uint32_t *__restrict__ tcell)
+{
+    Frame F;
+    const float tshift = FLUID_TARGETS ? 0.0f : (float)(int)(tcell[I.i] - I.c) * P.s_hf;
+    F.x = fmaf(fa.x, P.invhf, tshift);
+    F.y = fa.y * P.invhf;
+    F.z = fa.z * P.invhf;
+    F.thr = I.active ? 4.0004f - fmaf(F.x, F.x, fmaf(F.y, F.y, F.z * F.z)) : -INFINITY;
+    return F;
+}
+
+// Steps 1-4 above; hit(j, blist) runs for every hit of this lane (blist:
+// candidate j of the boundary list).  Every lane of the warp must call it.
+template <bool FLUID_TARGETS, class Hit>
+__device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int lane, const Item &I,
+                                             const Frame &F, const int32_t *__restrict__ fstart,
+                                             const float4 *__restrict__ fposf,
+                                             const int32_t *__restrict__ bstart,
+                                             const float4 *__restrict__ bposf,
+                                             const uint32_t *__restrict__ fcell, Hit &&hit)
+{
+    const int nlists = FLUID_TARGETS ? 2 : 1;
+    int K;
+    {
+        const int r = lane;
+        int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
+        if (r < 9 * nlists) {
+            const int list = r / 9, q = r % 9;
+            const int dz = q / 3 - 1, dy = q % 3 - 1;
+            const int y = I.cy + dy, z = I.cz + dz;
+            code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
+            if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
+                const int32_t *st = list ? bstart : fstart;
+                const int row = P.nx * (y + P.ny * z);
+                const int x0 = max(I.cx - 1, 0), x1 = min(I.cx1 + 1, P.nx - 1);
+                j0 = st[row + x0];
+                L = st[row + x1 + 1] - j0;
+                if (FLUID_TARGETS) {
+                    b1 = st[row + I.cx];       // first index of cell x
+                    b2 = st[row + I.cx + 1];   // first index of cell x + 1
+                } else {
+                    b1 = row + I.cx;           // cell id of the item's first cell in this row
+                }
+            }
+        }
+        int pe = L;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, pe, o);
+            if (lane >= o) pe += t;
+        }
+        if (r < NRUN) {
+            S.run[r] = make_int4(pe, j0, b1, b2);
+            S.code[r] = code;
+        }
+        K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
+    }
+    __syncwarp();
+
+    const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
+    const int npass = (K + CAP - 1) / CAP;
+    for (int pass = 0; pass < npass; ++pass) {
+        const int np = (K - pass + npass - 1) / npass;
+        const int nch = (np + 31) >> 5;
+        int r = 0;
+        for (int m = 0; m < nch; ++m) {
+            const int ls = lane + 32 * m;
+            const int sidx = ls < np ? pass + npass * ls : K;
+            float4 a;
+            uint32_t jj = 0;
+            if (sidx < K) {
+                while (sidx >= S.run[r].x) ++r;
+                const int4 ri = S.run[r];
+                const int prev = r ? S.run[r - 1].x : 0;
+                const int j = ri.y + (sidx - prev);
+                const int cd = S.code[r];
+                const float sx = FLUID_TARGETS
+                                     ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
+                                     : (float)((int)fcell[j] - ri.z) * P.s_hf;
+                const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
+                const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
+                const bool blist = FLUID_TARGETS && (cd & 1);
+                const float4 f = blist ? bposf[j] : fposf[j];
+                a.x = fmaf(f.x, P.invhf, sx);
+                a.y = fmaf(f.y, P.invhf, sy);
+                a.z = fmaf(f.z, P.invhf, sz);
+                a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+                jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
+            } else {
+                a = make_float4(0.f, 0.f, 0.f, INFINITY);
+            }
+            S.A[ls] = a;
+            S.J[ls] = jj;
+        }
+        __syncwarp();
+        // lockstep tests: the sign of t - thr is the hit bit, shifted into two
+        // 16-candidate masks that are joined and bit-reversed (candidate k at bit k)
+        for (int q = 0; q < nch; ++q) {
+            uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float4 a = S.A[q * 32 + k];
+                const float4 b = S.A[q * 32 + 16 + k];
+                const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
+                const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
+                lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+                hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+            }
+            S.M[q][lane] = __brev((lo << 16) | hi);
+        }
+        int q = 0;
+        uint32_t m = S.M[0][lane];
+        for (;;) {
+            while (m == 0u && q + 1 < nch) {
+                ++q;
+                m = S.M[q][lane];
+            }
+            if (m == 0u) break;
+            const int ls = q * 32 + __ffs(m) - 1;
+            m &= m - 1u;
+            const uint32_t jj = S.J[ls];
+            hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
+        }
+        __syncwarp();
+    }
+}
+
+}  // namespace witems
+}  // namespace sph
