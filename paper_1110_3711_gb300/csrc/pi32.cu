@@ -58,6 +58,7 @@ constexpr int CAP = SPH_PI_CAP;   // staged candidates per warp and pass
 constexpr int NCH = CAP / 32;     // 32-candidate chunks per pass
 constexpr int WARPS = SPH_PI_WARPS;
 constexpr int NRUN = 18;          // 9 fluid + 9 boundary x-runs
+constexpr int RAW_PER_PASS = CAP * 3 / 2;  // candidates sampled per pass (before the box test)
 static_assert(CAP % 32 == 0, "CAP must be a multiple of 32");
 
 struct WarpSmem {
@@ -67,6 +68,7 @@ struct WarpSmem {
     uint32_t M[NCH][32];  // hit bits of lane l for chunk q
     int4 run[NRUN];       // {inclusive end slot, first index, start of cell x, start of cell x+1}
     int code[NRUN];       // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
+    float box[6];         // targets' bounding box: min x, max x, min y, max y, min z, max z
 };
 
 struct Acc {
@@ -229,86 +231,126 @@ __device__ __forceinline__ void pi32_item(
         }
         __syncwarp();
 
+        // bounding box of the item's targets (units of h, item frame)
+        float bx0 = active ? xa : INFINITY, bx1 = active ? xa : -INFINITY;
+        float by0 = active ? ya : INFINITY, by1 = active ? ya : -INFINITY;
+        float bz0 = active ? za : INFINITY, bz1 = active ? za : -INFINITY;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            bx0 = fminf(bx0, __shfl_xor_sync(0xffffffffu, bx0, o));
+            bx1 = fmaxf(bx1, __shfl_xor_sync(0xffffffffu, bx1, o));
+            by0 = fminf(by0, __shfl_xor_sync(0xffffffffu, by0, o));
+            by1 = fmaxf(by1, __shfl_xor_sync(0xffffffffu, by1, o));
+            bz0 = fminf(bz0, __shfl_xor_sync(0xffffffffu, bz0, o));
+            bz1 = fmaxf(bz1, __shfl_xor_sync(0xffffffffu, bz1, o));
+        }
+        if (lane == 0) {
+            S.box[0] = bx0; S.box[1] = bx1;
+            S.box[2] = by0; S.box[3] = by1;
+            S.box[4] = bz0; S.box[5] = bz1;
+        }
+        __syncwarp();
+
         Acc o = {0.f, 0.f, 0.f, 0.f, 0.f};
-        // Pass p stages candidates p, p + npass, p + 2 npass, ...: every pass
+        // Pass p takes candidates p, p + npass, p + 2 npass, ...: every pass
         // samples the whole neighbourhood, so every lane finds about 1/npass of
-        // its neighbours in each pass and the hit walks stay balanced.
-        const int npass = (K + CAP - 1) / CAP;
+        // its neighbours in each pass and the hit walks stay balanced.  Only
+        // candidates within 2h of the targets' bounding box are staged (the
+        // others cannot be within 2h of any target; the box test's threshold
+        // 4.0004 h^2 lies above its float32 error and that of the lockstep
+        // test), packed with a ballot; the staged set is tested and walked
+        // whenever it may not take another 32.
+        const int npass = (K + RAW_PER_PASS - 1) / RAW_PER_PASS;
         for (int pass = 0; pass < npass; ++pass) {
             const int np = (K - pass + npass - 1) / npass;
-            const int nch = (np + 31) >> 5;
-            // ---- stage the candidates of this pass
-            int r = 0;
-            for (int m = 0; m < nch; ++m) {
-                const int ls = lane + 32 * m;
-                const int s = ls < np ? pass + npass * ls : K;
-                float4 a, v;
-                float pr;
-                if (s < K) {
-                    while (s >= S.run[r].x) ++r;
-                    const int4 ri = S.run[r];
-                    const int prev = r ? S.run[r - 1].x : 0;
-                    const int j = ri.y + (s - prev);
-                    const int cd = S.code[r];
-                    const float sx = MOMENTUM ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
-                                              : (float)((int)fcell[j] - ri.z) * P.s_hf;
-                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-                    float4 p;
-                    if (MOMENTUM && (cd & 1)) {
-                        p = bposp[j];
-                        v = bvelr[j];
-                    } else {
-                        p = fposp[j];
-                        v = fvelr[j];
+            int k0 = 0, r = 0;
+            while (k0 < np) {
+                // ---- stage the candidates near the box, at most CAP
+                int n = 0;
+                while (k0 < np && n <= CAP - 32) {
+                    const int ls = k0 + lane;
+                    bool keep = false;
+                    float4 a, v;
+                    float pr = 0.f;
+                    if (ls < np) {
+                        const int sidx = pass + npass * ls;
+                        while (sidx >= S.run[r].x) ++r;
+                        const int4 ri = S.run[r];
+                        const int prev = r ? S.run[r - 1].x : 0;
+                        const int j = ri.y + (sidx - prev);
+                        const int cd = S.code[r];
+                        const float sx =
+                            MOMENTUM ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
+                                     : (float)((int)fcell[j] - ri.z) * P.s_hf;
+                        const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
+                        const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
+                        const bool blist = MOMENTUM && (cd & 1);
+                        const float4 p = blist ? bposp[j] : fposp[j];
+                        a.x = fmaf(p.x, P.invhf, sx);
+                        a.y = fmaf(p.y, P.invhf, sy);
+                        a.z = fmaf(p.z, P.invhf, sz);
+                        const float dx = fmaxf(fmaxf(S.box[0] - a.x, a.x - S.box[1]), 0.0f);
+                        const float dy = fmaxf(fmaxf(S.box[2] - a.y, a.y - S.box[3]), 0.0f);
+                        const float dz = fmaxf(fmaxf(S.box[4] - a.z, a.z - S.box[5]), 0.0f);
+                        keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0004f;
+                        if (keep) {
+                            a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+                            v = blist ? bvelr[j] : fvelr[j];
+                            pr = p.w;
+                        }
                     }
-                    a.x = fmaf(p.x, P.invhf, sx);
-                    a.y = fmaf(p.y, P.invhf, sy);
-                    a.z = fmaf(p.z, P.invhf, sz);
-                    a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                    pr = p.w;
-                } else {
-                    a = make_float4(0.f, 0.f, 0.f, INFINITY);
-                    v = make_float4(0.f, 0.f, 0.f, 1.f);
-                    pr = 0.f;
+                    const unsigned ball = __ballot_sync(0xffffffffu, keep);
+                    if (keep) {
+                        const int slot = n + __popc(ball & ((1u << lane) - 1u));
+                        S.A[slot] = a;
+                        S.V[slot] = v;
+                        S.Pr[slot] = pr;
+                    }
+                    n += __popc(ball);
+                    k0 += 32;
                 }
-                S.A[ls] = a;
-                S.V[ls] = v;
-                S.Pr[ls] = pr;
-            }
-            __syncwarp();
-            // ---- lockstep distance tests, one hit bit per candidate
-            for (int q = 0; q < nch; ++q) {
-                // the sign of t - thr is the hit bit; it is shifted into two
-                // independent 16-candidate masks (candidate k lands at bit 15 - k
-                // of its half), which are joined and bit-reversed so that
-                // candidate k ends at bit k
-                uint32_t lo = 0u, hi = 0u;
+                // far candidates fill the last chunk
+                const int nch = (n + 31) >> 5;
+                if (n + lane < nch * 32) {
+                    S.A[n + lane] = make_float4(0.f, 0.f, 0.f, INFINITY);
+                    S.V[n + lane] = make_float4(0.f, 0.f, 0.f, 1.f);
+                    S.Pr[n + lane] = 0.f;
+                }
+                __syncwarp();
+                // ---- lockstep distance tests, one hit bit per candidate
+                for (int q = 0; q < nch; ++q) {
+                    // the sign of t - thr is the hit bit; it is shifted into two
+                    // independent 16-candidate masks (candidate k lands at bit 15 - k
+                    // of its half), which are joined and bit-reversed so that
+                    // candidate k ends at bit k
+                    uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float4 a = S.A[q * 32 + k];
-                    const float4 b = S.A[q * 32 + 16 + k];
-                    const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - thr;
-                    const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - thr;
-                    lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-                    hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+                    for (int k = 0; k < 16; ++k) {
+                        const float4 a = S.A[q * 32 + k];
+                        const float4 b = S.A[q * 32 + 16 + k];
+                        const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - thr;
+                        const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - thr;
+                        lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+                        hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+                    }
+                    S.M[q][lane] = __brev((lo << 16) | hi);
                 }
-                S.M[q][lane] = __brev((lo << 16) | hi);
-            }
-            // ---- every lane walks its own hits (about 112 per lane in all)
-            int q = 0;
-            uint32_t m = S.M[0][lane];
-            for (;;) {
-                while (m == 0u && q + 1 < nch) {
-                    ++q;
-                    m = S.M[q][lane];
+                // ---- every lane walks its own hits (about 112 per lane in all)
+                int q = 0;
+                uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
+                for (;;) {
+                    while (m == 0u && q + 1 < nch) {
+                        ++q;
+                        m = S.M[q][lane];
+                    }
+                    if (m == 0u) break;
+                    const int ls = q * 32 + __ffs(m) - 1;
+                    m &= m - 1u;
+                    pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, cpa, S.A[ls], S.V[ls],
+                                            S.Pr[ls], o);
                 }
-                if (m == 0u) break;
-                const int ls = q * 32 + __ffs(m) - 1;
-                m &= m - 1u;
-                pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, cpa, S.A[ls], S.V[ls], S.Pr[ls], o);
+                __syncwarp();
             }
-            __syncwarp();
         }
 
         if (active) {
