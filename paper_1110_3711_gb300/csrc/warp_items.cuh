@@ -8,18 +8,19 @@
 //      (dy, dz) of the 9 neighbour rows, cells x-1 .. x+1 (of the item's first
 //      and last cell) are one index range of the fluid list, and for fluid
 //      targets of the boundary list too;
-//   2. stages the candidates of those runs in shared memory as their float32
-//      cell-relative offsets shifted into the frame of the item's first cell,
-//      in units of h, with |x|^2 beside them, and their indices;
+//   2. stages the candidates of those runs that lie within 2h of the targets'
+//      bounding box in shared memory, as their float32 cell-relative offsets
+//      shifted into the frame of the item's first cell, in units of h, with
+//      |x|^2 beside them, and their indices;
 //   3. tests every candidate against every target in lockstep, in float32,
 //      against 4 (1 + 1e-4) (units of h^2): the float32 error of the offsets
 //      and of the test is below 1e-5 of 4, so every pair of the float64 test
 //      r^2 < 4h^2 is a hit (the float64 test then decides);
 //   4. lets every lane walk its own hits in staging order, calling the
 //      caller's hit function with the candidate's index and list.
-// Neighbourhoods of more than CAP candidates take several passes; pass p
-// stages candidates p, p + npass, ..., so that each pass holds about 1/npass
-// of every lane's neighbours.  The walk order depends only on the item, so
+// Neighbourhoods of more candidates than a pass holds take several passes;
+// pass p samples candidates p, p + npass, ..., so that each pass holds about
+// 1/npass of every lane's neighbours.  The walk order depends only on the item, so
 // sums accumulated in it are deterministic.  Cells of edge 2h or more only.
 #pragma once
 
@@ -32,12 +33,15 @@ constexpr int CAP = 256;
 constexpr int NCH = CAP / 32;
 constexpr int NRUN = 18;   // 9 fluid + 9 boundary x-runs
 
+constexpr int RAW_PER_PASS = CAP * 3 / 2;  // candidates sampled per pass (before the box test)
+
 struct Smem {
     float4 A[CAP];          // shifted offset {x, y, z} (units of h) and |x|^2
     uint32_t J[CAP];        // candidate index, bit 31 set for the boundary list
     uint32_t M[NCH][32];    // hit bits of lane l for chunk q
     int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
     int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
+    float box[6];           // targets' bounding box: min x, max x, min y, max y, min z, max z
 };
 
 // The item's targets as one lane sees them.
@@ -140,71 +144,113 @@ __device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int la
     }
     __syncwarp();
 
+    // bounding box of the item's targets (units of h, item frame)
+    {
+        const bool act = F.thr > -INFINITY;
+        float b[6] = {act ? F.x : INFINITY, act ? F.x : -INFINITY, act ? F.y : INFINITY,
+                      act ? F.y : -INFINITY, act ? F.z : INFINITY, act ? F.z : -INFINITY};
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                b[2 * d] = fminf(b[2 * d], __shfl_xor_sync(0xffffffffu, b[2 * d], o));
+                b[2 * d + 1] = fmaxf(b[2 * d + 1], __shfl_xor_sync(0xffffffffu, b[2 * d + 1], o));
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int d = 0; d < 6; ++d) S.box[d] = b[d];
+        }
+        __syncwarp();
+    }
+
     const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
-    const int npass = (K + CAP - 1) / CAP;
+    // Pass p takes candidates p, p + npass, ... (an interleaved sample of the
+    // whole neighbourhood); only those within 2h of the targets' bounding box
+    // are staged (the box test's threshold 4.0004 h^2 lies above its float32
+    // error), packed with a ballot, and the staged set is tested and walked
+    // whenever it may not take another 32.
+    const int npass = (K + RAW_PER_PASS - 1) / RAW_PER_PASS;
     for (int pass = 0; pass < npass; ++pass) {
         const int np = (K - pass + npass - 1) / npass;
-        const int nch = (np + 31) >> 5;
-        int r = 0;
-        for (int m = 0; m < nch; ++m) {
-            const int ls = lane + 32 * m;
-            const int sidx = ls < np ? pass + npass * ls : K;
-            float4 a;
-            uint32_t jj = 0;
-            if (sidx < K) {
-                while (sidx >= S.run[r].x) ++r;
-                const int4 ri = S.run[r];
-                const int prev = r ? S.run[r - 1].x : 0;
-                const int j = ri.y + (sidx - prev);
-                const int cd = S.code[r];
-                const float sx = FLUID_TARGETS
-                                     ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
-                                     : (float)((int)fcell[j] - ri.z) * P.s_hf;
-                const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-                const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-                const bool blist = FLUID_TARGETS && (cd & 1);
-                const float4 f = blist ? bposf[j] : fposf[j];
-                a.x = fmaf(f.x, P.invhf, sx);
-                a.y = fmaf(f.y, P.invhf, sy);
-                a.z = fmaf(f.z, P.invhf, sz);
-                a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
-            } else {
-                a = make_float4(0.f, 0.f, 0.f, INFINITY);
+        int k0 = 0, r = 0;
+        while (k0 < np) {
+            int n = 0;
+            while (k0 < np && n <= CAP - 32) {
+                const int ls = k0 + lane;
+                bool keep = false;
+                float4 a;
+                uint32_t jj = 0;
+                if (ls < np) {
+                    const int sidx = pass + npass * ls;
+                    while (sidx >= S.run[r].x) ++r;
+                    const int4 ri = S.run[r];
+                    const int prev = r ? S.run[r - 1].x : 0;
+                    const int j = ri.y + (sidx - prev);
+                    const int cd = S.code[r];
+                    const float sx = FLUID_TARGETS
+                                         ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
+                                         : (float)((int)fcell[j] - ri.z) * P.s_hf;
+                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
+                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
+                    const bool blist = FLUID_TARGETS && (cd & 1);
+                    const float4 f = blist ? bposf[j] : fposf[j];
+                    a.x = fmaf(f.x, P.invhf, sx);
+                    a.y = fmaf(f.y, P.invhf, sy);
+                    a.z = fmaf(f.z, P.invhf, sz);
+                    const float dx = fmaxf(fmaxf(S.box[0] - a.x, a.x - S.box[1]), 0.0f);
+                    const float dy = fmaxf(fmaxf(S.box[2] - a.y, a.y - S.box[3]), 0.0f);
+                    const float dz = fmaxf(fmaxf(S.box[4] - a.z, a.z - S.box[5]), 0.0f);
+                    keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0004f;
+                    a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+                    jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
+                }
+                const unsigned ball = __ballot_sync(0xffffffffu, keep);
+                if (keep) {
+                    const int slot = n + __popc(ball & ((1u << lane) - 1u));
+                    S.A[slot] = a;
+                    S.J[slot] = jj;
+                }
+                n += __popc(ball);
+                k0 += 32;
             }
-            S.A[ls] = a;
-            S.J[ls] = jj;
-        }
-        __syncwarp();
-        // lockstep tests: the sign of t - thr is the hit bit, shifted into two
-        // 16-candidate masks that are joined and bit-reversed (candidate k at bit k)
-        for (int q = 0; q < nch; ++q) {
-            uint32_t lo = 0u, hi = 0u;
+            // far candidates fill the last chunk
+            const int nch = (n + 31) >> 5;
+            if (n + lane < nch * 32) {
+                S.A[n + lane] = make_float4(0.f, 0.f, 0.f, INFINITY);
+                S.J[n + lane] = 0u;
+            }
+            __syncwarp();
+            // lockstep tests: the sign of t - thr is the hit bit, shifted into two
+            // 16-candidate masks that are joined and bit-reversed (candidate k at bit k)
+            for (int q = 0; q < nch; ++q) {
+                uint32_t lo = 0u, hi = 0u;
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                const float4 a = S.A[q * 32 + k];
-                const float4 b = S.A[q * 32 + 16 + k];
-                const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
-                const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
-                lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-                hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+                for (int k = 0; k < 16; ++k) {
+                    const float4 a = S.A[q * 32 + k];
+                    const float4 b = S.A[q * 32 + 16 + k];
+                    const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
+                    const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
+                    lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+                    hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+                }
+                S.M[q][lane] = __brev((lo << 16) | hi);
             }
-            S.M[q][lane] = __brev((lo << 16) | hi);
-        }
-        int q = 0;
-        uint32_t m = S.M[0][lane];
-        for (;;) {
-            while (m == 0u && q + 1 < nch) {
-                ++q;
-                m = S.M[q][lane];
+            int q = 0;
+            uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
+            for (;;) {
+                while (m == 0u && q + 1 < nch) {
+                    ++q;
+                    m = S.M[q][lane];
+                }
+                if (m == 0u) break;
+                const int ls = q * 32 + __ffs(m) - 1;
+                m &= m - 1u;
+                const uint32_t jj = S.J[ls];
+                hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
             }
-            if (m == 0u) break;
-            const int ls = q * 32 + __ffs(m) - 1;
-            m &= m - 1u;
-            const uint32_t jj = S.J[ls];
-            hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
+            __syncwarp();
         }
-        __syncwarp();
     }
 }
 
