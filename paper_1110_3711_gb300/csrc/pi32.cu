@@ -58,7 +58,7 @@ constexpr int CAP = SPH_PI_CAP;   // staged candidates per warp and pass
 constexpr int NCH = CAP / 32;     // 32-candidate chunks per pass
 constexpr int WARPS = SPH_PI_WARPS;
 constexpr int NRUN = 18;          // 9 fluid + 9 boundary x-runs
-constexpr int RAW_PER_PASS = CAP * 3 / 2;  // candidates sampled per pass (before the box test)
+constexpr int RAW_PER_PASS = 2 * CAP;  // candidates sampled per pass (before the box test)
 static_assert(CAP % 32 == 0, "CAP must be a multiple of 32");
 
 struct WarpSmem {

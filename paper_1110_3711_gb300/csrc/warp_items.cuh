@@ -33,7 +33,7 @@ constexpr int CAP = 256;
 constexpr int NCH = CAP / 32;
 constexpr int NRUN = 18;   // 9 fluid + 9 boundary x-runs
 
-constexpr int RAW_PER_PASS = CAP * 3 / 2;  // candidates sampled per pass (before the box test)
+constexpr int RAW_PER_PASS = 2 * CAP;  // candidates sampled per pass (before the box test)
 
 struct Smem {
     float4 A[CAP];          // shifted offset {x, y, z} (units of h) and |x|^2
