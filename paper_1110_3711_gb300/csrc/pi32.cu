@@ -285,7 +285,10 @@ __device__ __forceinline__ void pi32_item(
                         const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
                         const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
                         const bool blist = MOMENTUM && (cd & 1);
+                        // both loads issued together (the velocity is wasted on a
+                        // candidate the box test drops, but waits on nothing)
                         const float4 p = blist ? bposp[j] : fposp[j];
+                        v = blist ? bvelr[j] : fvelr[j];
                         a.x = fmaf(p.x, P.invhf, sx);
                         a.y = fmaf(p.y, P.invhf, sy);
                         a.z = fmaf(p.z, P.invhf, sz);
@@ -295,7 +298,6 @@ __device__ __forceinline__ void pi32_item(
                         keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0004f;
                         if (keep) {
                             a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                            v = blist ? bvelr[j] : fvelr[j];
                             pr = p.w;
                         }
                     }
