@@ -337,6 +337,10 @@ __device__ __forceinline__ void pi32_item(
                     }
                     S.M[q][lane] = __brev((lo << 16) | hi);
                 }
+                // |x|^2 has served the tests: the pair walk reads P/rho^2 from its place
+                __syncwarp();
+                for (int q2 = 0; q2 < nch; ++q2) S.A[q2 * 32 + lane].w = S.Pr[q2 * 32 + lane];
+                __syncwarp();
                 // ---- every lane walks its own hits (about 112 per lane in all)
                 int q = 0;
                 uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
@@ -348,8 +352,8 @@ __device__ __forceinline__ void pi32_item(
                     if (m == 0u) break;
                     const int ls = q * 32 + __ffs(m) - 1;
                     m &= m - 1u;
-                    pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, cpa, S.A[ls], S.V[ls],
-                                            S.Pr[ls], o);
+                    const float4 b = S.A[ls];
+                    pair<MOMENTUM, TENSILE>(P, xa, ya, za, pa, va, cpa, b, S.V[ls], b.w, o);
                 }
                 __syncwarp();
             }
