@@ -305,19 +305,30 @@ def e2e_form(torch, sim, steps):
                 note="state uploaded from and read back to pinned host memory every step")
 
 
+def code_hash(path):
+    """sha256 (16 hex digits) of a C/CUDA source with its comments and
+    whitespace removed: edits of comments do not change it, edits of code do."""
+    import re
+    src = open(path, encoding="utf-8").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    src = re.sub(r"\s+", "", src)
+    return hashlib.sha256(src.encode()).hexdigest()[:16]
+
+
 def traffic_from_profiles(kernel_src):
     """DRAM bytes per PI call from the committed ncu summary, if it was taken on
     the current kernel source; else None."""
     path = os.path.join(ROOT, "profiles", "pi_dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    sha = code_hash(kernel_src)
     vals = {}
     for ln in open(path):
         if "=" in ln and not ln.startswith("#"):
             k, v = ln.split("=", 1)
             vals[k.strip()] = v.strip()
-    if vals.get("pi_cu_sha256_16") != sha:
+    if vals.get("pi_cu_code_sha256_16") != sha:
         return None
     try:
         return float(vals["dram_bytes_per_pi_call"])

@@ -9,9 +9,11 @@
 //   1. builds the table of its 9 fluid x-runs (and 9 boundary x-runs for
 //      fluid targets): cells x-1..x+1 of every (y, z) row are one index range
 //      (Section 4.4, Fig. 10);
-//   2. stages the candidates of those runs in shared memory, already shifted
-//      into the frame of the target cell and measured in units of h
-//      ((candidate offset + cell delta * s) / h), with |x_b|^2 beside them;
+//   2. stages the candidates of those runs that lie within 2h of the bounding
+//      box of its targets (the others cannot be neighbours of any of them) in
+//      shared memory, already shifted into the frame of the target cell and
+//      measured in units of h ((candidate offset + cell delta * s) / h), with
+//      |x_b|^2 beside them;
 //   3. tests all candidates against all 32 targets in lockstep: the warp reads
 //      one candidate (a shared-memory broadcast) and each lane evaluates
 //      |x_b|^2 - 2 x_a.x_b - (4 - |x_a|^2) (three FMAs and a subtraction; it
