@@ -1,9 +1,13 @@
 // PI stage (Sections 2, 4.3-4.5 of the paper): particle interactions.
 //
-// One thread per target particle (Section 4): its own data stay in registers
-// and its sums are written once at the end (Section 4.5).  Fluid targets
-// evaluate F-F and F-B in one kernel (Section 4.5, optimisation E); boundary
-// targets have their own B-F kernel (continuity only).  Candidates are the
+// Float64 form, two designs.  k_pi64w (default for cells of edge 2h or more):
+// one warp per work item with float32 lockstep candidate tests and float64
+// pairs in per-lane hit walks (warp_items.cuh), fluid and boundary items in
+// one launch.  k_pi_fluid64 / k_pi_boundary64: one thread per target particle
+// (Section 4): its own data stay in registers and its sums are written once at
+// the end (Section 4.5); fluid targets evaluate F-F and F-B in one kernel
+// (Section 4.5, optimisation E), boundary targets have their own B-F kernel
+// (continuity only).  Candidates are the
 // particles of the 27 surrounding cells, visited as the 9 x-runs of Fig. 10 /
 // Fig. 11 (cells x-1, x, x+1 of one (y, z) row are contiguous after NL); with
 // cells of edge in [h, 2h) (the paper's finer cells, Section 4.6, optimisation F) the 125
