@@ -6,13 +6,14 @@
  *
  * One time step is the paper's three stages (Section 2, Fig. 1), each a call:
  *   sph_neighbour_list  NL  cell-linked list: cell of every fluid particle, a
- *                           radix sort by (cell, id), reordering of all particle
- *                           data, first particle of every cell (Sections 2, 4.1,
+ *                           sort by (cell, id), reordering of all particle data,
+ *                           first particle of every cell (Sections 2, 4.1,
  *                           Fig. 8);
- *   sph_interact        PI  fluid-fluid + fluid-boundary interactions in one
- *                           kernel and boundary-fluid in a second one (Section
- *                           4.5): momentum and continuity with the cubic spline,
- *                           Tait pressure and artificial viscosity (Table 1);
+ *   sph_interact        PI  fluid-fluid + fluid-boundary interactions of fluid
+ *                           targets and boundary-fluid interactions of boundary
+ *                           targets (Section 4.5): momentum and continuity with
+ *                           the cubic spline, Tait pressure and artificial
+ *                           viscosity (Table 1);
  *   sph_update          SU  variable time step from the largest force, sound
  *                           speed and viscous term (Section 4.1, Table 1) and
  *                           the Verlet scheme with a periodic Euler step (Table 1).
@@ -142,9 +143,10 @@ int sph_create(const sph_params *p, int64_t n_f, int64_t n_b,
                const double *pos, const double *vel, const double *rho,
                void *workspace, size_t ws_bytes, void *stream, sph_ctx **out);
 
-/* NL (Section 4.1): cell of every fluid particle, stable LSD radix sort by
- * (cell, id), gather of all fluid arrays into the new order, packed PI inputs
- * (Section 4.3) and the first index of every cell.  Asynchronous. */
+/* NL (Section 4.1): cell of every fluid particle, sort by (cell, id) (a
+ * counting sort by cell, then the rank by id inside each cell), all fluid
+ * arrays copied into that order, packed PI inputs (Section 4.3), the first
+ * index of every cell and the PI work items.  Asynchronous. */
 int sph_neighbour_list(sph_ctx *ctx);
 
 /* PI (Sections 4.3-4.5): forces and density rates of every particle from its
