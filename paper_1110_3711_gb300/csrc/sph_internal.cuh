@@ -91,7 +91,7 @@ struct Workspace {
     // cell-grouped order.  Boundary: the radix sort's keys and values.
     uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
     uint32_t *count;          // [ncells + 2], then the work-item counters ctr
-    uint32_t *ctr;            // [0] fluid items, [1] fluid next, [2] boundary next, [3] boundary items
+    uint32_t *ctr;            // [0] fluid items, [1] next item of the PI queue, [2] spare, [3] boundary items
     uint32_t *items_f, *items_b;  // PI work items: fluid, first target of a (cell, 32-target chunk);
                                   // boundary, {first, count} of packed cells of one x row
     int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
