@@ -567,7 +567,12 @@ def main():
         "fp64": (None if r64 is None else
                  {"steps_per_s": r64["steps_per_s"], "ms_per_step": r64["ms_per_step"],
                   "interactions_per_s": r64["interactions_per_s"], "steps": args.fp64_steps,
-                  "stage_ms": r64["stage_ms"]}),
+                  "stage_ms": r64["stage_ms"],
+                  # the same FLOP count in float64 over the measured float64 FMA rate
+                  "pi_tflops": pi_flops(r64["counts"]) / (r64["pi_ms"] / 1e3) / 1e12,
+                  "pi_frac_of_measured_fp64_fma": (
+                      pi_flops(r64["counts"]) / (r64["pi_ms"] / 1e3) / 1e12 / fma["fp64_tflops"]
+                      if fma.get("fp64_tflops") else None)}),
         "fp32_over_fp64": None if r64 is None else r32["steps_per_s"] / r64["steps_per_s"],
         "roofline": {"bound": "alu",
                      "kernel": "PI (sph_interact: k_pi32, fluid and boundary work items)",
