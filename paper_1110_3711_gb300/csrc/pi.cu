@@ -304,25 +304,46 @@ __device__ __forceinline__ void pi64_item(
     const int32_t *__restrict__ fstart, const double4_32a *__restrict__ bposp,
     const double4_32a *__restrict__ bvelr, const float4 *__restrict__ bposf,
     const int32_t *__restrict__ bstart, const uint32_t *__restrict__ fcell,
-    double4_32a *__restrict__ acc, double *__restrict__ bar, double &f2max, double &vismax,
-    bool &bad)
+    double4_32a *__restrict__ acc, double *__restrict__ bar, double *part, double &f2max,
+    double &vismax, bool &bad)
 {
     const witems::Item I = witems::item_of<MOMENTUM>(P, items, it, tcell, tstart, lane);
     const int i = I.i;
-    const double4_32a pa = tposp[i], va = tvelr[i];
     const witems::Frame Fr = witems::frame_of<MOMENTUM>(P, I, tposf[i], tcell);
-    const double ca = MOMENTUM ? sound64(P, va.w) : 0.0;
     const double s2 = 4.0 * P.h * P.h;
-    Acc64 o = {0.0, 0.0, 0.0, 0.0, 0.0};
-    witems::for_each_hit<MOMENTUM>(P, S, lane, I, Fr, fstart, fposf, bstart, bposf, fcell,
-                                   [&](int j, bool blist) {
-        if (MOMENTUM && !blist && j == i) return;   // the target itself
-        const double4_32a pb = blist ? bposp[j] : fposp[j];
-        const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
-        const double r2 = rx * rx + ry * ry + rz * rz;
-        if (r2 < s2)
-            pair64<MOMENTUM>(P, pa, va, ca, pb, blist ? bvelr[j] : fvelr[j], rx, ry, rz, r2, o);
-    });
+    // the target this lane works for in the balanced walk, its sums, and the
+    // lane's own target's total
+    int wi = i;
+    double4_32a pa, va;
+    double ca = 0.0;
+    Acc64 w = {0.0, 0.0, 0.0, 0.0, 0.0}, o = {0.0, 0.0, 0.0, 0.0, 0.0};
+    witems::for_each_hit_balanced<MOMENTUM>(
+        P, S, lane, I, Fr, fstart, fposf, bstart, bposf, fcell,
+        [&](int t) {
+            wi = I.i0 + t;
+            pa = tposp[wi];
+            va = tvelr[wi];
+            ca = MOMENTUM ? sound64(P, va.w) : 0.0;
+            w = {0.0, 0.0, 0.0, 0.0, 0.0};
+        },
+        [&](int j, bool blist) {
+            if (MOMENTUM && !blist && j == wi) return;   // the target itself
+            const double4_32a pb = blist ? bposp[j] : fposp[j];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            const double r2 = rx * rx + ry * ry + rz * rz;
+            if (r2 < s2)
+                pair64<MOMENTUM>(P, pa, va, ca, pb, blist ? bvelr[j] : fvelr[j], rx, ry, rz, r2,
+                                 w);
+        },
+        [&](int, int slot) {
+            double *ps = part + 5 * slot;
+            ps[0] = w.ax; ps[1] = w.ay; ps[2] = w.az; ps[3] = w.ar; ps[4] = w.vis;
+        },
+        [&](int slot) {
+            const double *ps = part + 5 * slot;
+            o.ax += ps[0]; o.ay += ps[1]; o.az += ps[2]; o.ar += ps[3];
+            o.vis = fmax(o.vis, ps[4]);
+        });
     if (I.active) {
         if (MOMENTUM) {
             const double ax = P.mass * o.ax + P.g[0];
@@ -355,9 +376,11 @@ k_pi64w(DevParams P, int nf, int nb, const uint32_t *__restrict__ items_f,
         double4_32a *__restrict__ acc, double *__restrict__ bar, Scalars *sc)
 {
     __shared__ witems::Smem smem[W64_WARPS];
+    __shared__ double partsm[W64_WARPS][5 * witems::NSLOT];   // balanced-walk partial sums
     __shared__ double red[32];
     const int lane = threadIdx.x & 31;
     witems::Smem &S = smem[threadIdx.x >> 5];
+    double *part = partsm[threadIdx.x >> 5];
     const uint32_t nfi = ctr[0];
     const uint32_t n_items = nfi + (use_b ? ctr[3] : 0u);
     double f2max = 0.0, vismax = 0.0;
@@ -369,12 +392,12 @@ k_pi64w(DevParams P, int nf, int nb, const uint32_t *__restrict__ items_f,
         if (it >= n_items) break;
         if (it < nfi)
             pi64_item<true>(P, S, lane, it, items_f, posp, velr, posf, cell, fstart, posp, velr,
-                            posf, fstart, bposp, bvelr, bposf, bstart, cell, acc, bar, f2max,
-                            vismax, bad);
+                            posf, fstart, bposp, bvelr, bposf, bstart, cell, acc, bar, part,
+                            f2max, vismax, bad);
         else
             pi64_item<false>(P, S, lane, it - nfi, items_b, bposp, bvelr, bposf, bcell, bstart,
                              posp, velr, posf, fstart, nullptr, nullptr, nullptr, bstart, cell,
-                             acc, bar, f2max, vismax, bad);
+                             acc, bar, part, f2max, vismax, bad);
     }
     const int g = blockIdx.x * blockDim.x + threadIdx.x, G = gridDim.x * blockDim.x;
     for (int k = fstart[P.ncells] + g; k < nf; k += G) acc[k] = make_double4_32a(0.0, 0.0, 0.0, 0.0);

@@ -42,7 +42,10 @@ struct Smem {
     int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
     int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
     float box[6];           // targets' bounding box: min x, max x, min y, max y, min z, max z
+    int hincl[32];          // balanced walk: hits of targets 0 .. t of the tested set
 };
+
+constexpr int NSLOT = 63;   // partial-sum slots of the balanced walk (lane + target)
 
 // The item's targets as one lane sees them.
 struct Item {
@@ -96,15 +99,17 @@ __device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, con
     return F;
 }
 
-// Steps 1-4 above; hit(j, blist) runs for every hit of this lane (blist:
-// candidate j of the boundary list).  Every lane of the warp must call it.
-template <bool FLUID_TARGETS, class Hit>
-__device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int lane, const Item &I,
-                                             const Frame &F, const int32_t *__restrict__ fstart,
-                                             const float4 *__restrict__ fposf,
-                                             const int32_t *__restrict__ bstart,
-                                             const float4 *__restrict__ bposf,
-                                             const uint32_t *__restrict__ fcell, Hit &&hit)
+// Steps 1-3 above; after each staged set is tested, flush(nch) runs with the
+// hit masks of its nch chunks in S.M (lane l's bit k of S.M[q][l]: candidate
+// q * 32 + k is a hit of target l).  Every lane of the warp must call it.
+template <bool FLUID_TARGETS, class Flush>
+__device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int lane,
+                                               const Item &I, const Frame &F,
+                                               const int32_t *__restrict__ fstart,
+                                               const float4 *__restrict__ fposf,
+                                               const int32_t *__restrict__ bstart,
+                                               const float4 *__restrict__ bposf,
+                                               const uint32_t *__restrict__ fcell, Flush &&flush)
 {
     const int nlists = FLUID_TARGETS ? 2 : 1;
     int K;
@@ -236,22 +241,124 @@ __device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int la
                 }
                 S.M[q][lane] = __brev((lo << 16) | hi);
             }
+            __syncwarp();
+            flush(nch);
+            __syncwarp();
+        }
+    }
+}
+
+// Steps 1-4 above; hit(j, blist) runs for every hit of this lane (blist:
+// candidate j of the boundary list).  Every lane of the warp must call it.
+template <bool FLUID_TARGETS, class Hit>
+__device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int lane, const Item &I,
+                                             const Frame &F, const int32_t *__restrict__ fstart,
+                                             const float4 *__restrict__ fposf,
+                                             const int32_t *__restrict__ bstart,
+                                             const float4 *__restrict__ bposf,
+                                             const uint32_t *__restrict__ fcell, Hit &&hit)
+{
+    stage_and_test<FLUID_TARGETS>(P, S, lane, I, F, fstart, fposf, bstart, bposf, fcell,
+                                  [&](int nch) {
+        int q = 0;
+        uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
+        for (;;) {
+            while (m == 0u && q + 1 < nch) {
+                ++q;
+                m = S.M[q][lane];
+            }
+            if (m == 0u) break;
+            const int ls = q * 32 + __ffs(m) - 1;
+            m &= m - 1u;
+            const uint32_t jj = S.J[ls];
+            hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
+        }
+    });
+}
+
+// Steps 1-3 above, then a balanced walk: the hits of a tested set, taken in
+// target order (target t is lane t of the item) and staging order within a
+// target, are dealt to the 32 lanes in equal consecutive shares, so every
+// lane walks the same number of hits whatever the targets' counts (the
+// float64 pipe, which takes about 19 cycles per warp instruction on GB300,
+// then works with all lanes busy).  A lane whose share spans several targets
+// switches target in between:
+//   begin(t)        the lane now works for target t (load it, clear the sums);
+//   hit(j, blist)   a hit of that target;
+//   end(t, slot)    the lane's partial sums for t go to partial slot `slot`;
+// slots are lane + t, unique along the staircase the shares form.  Then the
+// lane of every target with hits adds its slots in lane order,
+//   combine(slot),
+// so the result depends only on the item, not on scheduling.
+template <bool FLUID_TARGETS, class Begin, class Hit, class End, class Combine>
+__device__ __forceinline__ void for_each_hit_balanced(
+    const DevParams &P, Smem &S, int lane, const Item &I, const Frame &F,
+    const int32_t *__restrict__ fstart, const float4 *__restrict__ fposf,
+    const int32_t *__restrict__ bstart, const float4 *__restrict__ bposf,
+    const uint32_t *__restrict__ fcell, Begin &&begin, Hit &&hit, End &&end, Combine &&combine)
+{
+    stage_and_test<FLUID_TARGETS>(P, S, lane, I, F, fstart, fposf, bstart, bposf, fcell,
+                                  [&](int nch) {
+        // hits per target and their inclusive prefix over the lanes
+        int c = 0;
+        for (int q = 0; q < nch; ++q) c += __popc(S.M[q][lane]);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        S.hincl[lane] = incl;
+        const int T = __shfl_sync(0xffffffffu, incl, 31);
+        __syncwarp();
+        if (T == 0) return;
+        const int sh = (T + 31) >> 5;
+        const int g0 = min(lane * sh, T), g1 = min(g0 + sh, T);
+        if (g0 < g1) {
+            // the target holding hit g0: the smallest t with incl[t] > g0
+            int lo = 0, hi = 31;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (S.hincl[mid] > g0) hi = mid;
+                else lo = mid + 1;
+            }
+            int t = lo;
+            int o = g0 - (t ? S.hincl[t - 1] : 0);   // hits of t before g0
             int q = 0;
-            uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
-            for (;;) {
-                while (m == 0u && q + 1 < nch) {
-                    ++q;
-                    m = S.M[q][lane];
+            uint32_t m = S.M[0][t];
+            while (o >= __popc(m)) {
+                o -= __popc(m);
+                m = S.M[++q][t];
+            }
+            for (; o > 0; --o) m &= m - 1u;
+            begin(t);
+            for (int g = g0; g < g1; ++g) {
+                while (m == 0u) {
+                    if (++q == nch) {
+                        end(t, lane + t);
+                        // the next target with hits (one exists: g < g1 <= T)
+                        do {
+                            ++t;
+                        } while (S.hincl[t] == S.hincl[t - 1]);
+                        begin(t);
+                        q = 0;
+                    }
+                    m = S.M[q][t];
                 }
-                if (m == 0u) break;
                 const int ls = q * 32 + __ffs(m) - 1;
                 m &= m - 1u;
                 const uint32_t jj = S.J[ls];
                 hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
             }
-            __syncwarp();
+            end(t, lane + t);
         }
-    }
+        __syncwarp();
+        // the target of this lane adds the partial sums of its shares in lane order
+        if (c > 0) {
+            const int first = incl - c, last = incl - 1;
+            for (int L = first / sh; L <= last / sh; ++L) combine(L + lane);
+        }
+    });
 }
 
 }  // namespace witems
