@@ -452,37 +452,65 @@ __device__ __forceinline__ void adj_fluid_item(
     const double4_32a *__restrict__ bposp, const double4_32a *__restrict__ bvelr,
     const float4 *__restrict__ bposf, const int32_t *__restrict__ bstart,
     const double *__restrict__ gF, const double *__restrict__ gD, double *__restrict__ lam_s,
-    double *__restrict__ part)
+    double *__restrict__ part, double *slots)
 {
     const witems::Item I = witems::item_of<true>(P, items, it, cell, fstart, lane);
     const int i = I.i;
-    const double4_32a pa = posp[i], va = velr[i];
-    const PartTerms ta = part_terms(P, va.w, pa.w);
-    const double gFx = gF[3 * (size_t)i], gFy = gF[3 * (size_t)i + 1],
-                 gFz = gF[3 * (size_t)i + 2], gDa = gD[i];
     const witems::Frame Fr = witems::frame_of<true>(P, I, posf[i], cell);
     const double s2 = 4.0 * P.h * P.h;
+    // the target this lane works for in the balanced walk, its sums (w), and
+    // the total of the lane's own target (l)
+    int wi = i;
+    double4_32a pa, va;
+    PartTerms ta;
+    double gFx = 0.0, gFy = 0.0, gFz = 0.0, gDa = 0.0;
+    SelfAdj w = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     SelfAdj l = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
-    witems::for_each_hit<true>(P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
-                               [&](int j, bool blist) {
-        if (!blist) {
-            if (j == i) return;
-            const double4_32a pb = posp[j];
-            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
-            if (!(rx * rx + ry * ry + rz * rz < s2)) return;
-            const double4_32a vb = velr[j];
-            pair_adj<true>(P, rx, ry, rz, va.x - vb.x, va.y - vb.y, va.z - vb.z, ta, vb.w, pb.w,
-                           sound_of(P, vb.w), gFx, gFy, gFz, gF[3 * (size_t)j],
-                           gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gDa + gD[j], l);
-        } else {
-            const double4_32a pb = bposp[j];
-            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
-            if (!(rx * rx + ry * ry + rz * rz < s2)) return;
-            const double rho_b = bvelr[j].w;
-            pair_adj<false>(P, rx, ry, rz, va.x, va.y, va.z, ta, rho_b, pb.w, sound_of(P, rho_b),
-                            gFx, gFy, gFz, 0.0, 0.0, 0.0, gDa + gD[(size_t)nf + j], l);
-        }
-    });
+    witems::for_each_hit_balanced<true>(
+        P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
+        [&](int t) {
+            wi = I.i0 + t;
+            pa = posp[wi];
+            va = velr[wi];
+            ta = part_terms(P, va.w, pa.w);
+            gFx = gF[3 * (size_t)wi];
+            gFy = gF[3 * (size_t)wi + 1];
+            gFz = gF[3 * (size_t)wi + 2];
+            gDa = gD[wi];
+            w = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        },
+        [&](int j, bool blist) {
+            if (!blist) {
+                if (j == wi) return;
+                const double4_32a pb = posp[j];
+                const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+                if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+                const double4_32a vb = velr[j];
+                pair_adj<true>(P, rx, ry, rz, va.x - vb.x, va.y - vb.y, va.z - vb.z, ta, vb.w,
+                               pb.w, sound_of(P, vb.w), gFx, gFy, gFz, gF[3 * (size_t)j],
+                               gF[3 * (size_t)j + 1], gF[3 * (size_t)j + 2], gDa + gD[j], w);
+            } else {
+                const double4_32a pb = bposp[j];
+                const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+                if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+                const double rho_b = bvelr[j].w;
+                pair_adj<false>(P, rx, ry, rz, va.x, va.y, va.z, ta, rho_b, pb.w,
+                                sound_of(P, rho_b), gFx, gFy, gFz, 0.0, 0.0, 0.0,
+                                gDa + gD[(size_t)nf + j], w);
+            }
+        },
+        [&](int, int slot) {
+            double *ps = slots + 8 * slot;
+            ps[0] = w.rx; ps[1] = w.ry; ps[2] = w.rz;
+            ps[3] = w.vx; ps[4] = w.vy; ps[5] = w.vz;
+            ps[6] = w.rho; ps[7] = w.alpha;
+        },
+        [&](int slot) {
+            const double *ps = slots + 8 * slot;
+            l.rx += ps[0]; l.ry += ps[1]; l.rz += ps[2];
+            l.vx += ps[3]; l.vy += ps[4]; l.vz += ps[5];
+            l.rho += ps[6]; l.alpha += ps[7];
+        });
     if (I.active) {
         double *ox = lam_s + 3 * (size_t)i, *ov = lam_s + 3 * N + 3 * (size_t)i;
         ox[0] += l.rx; ox[1] += l.ry; ox[2] += l.rz;
@@ -536,8 +564,10 @@ k_adj_pi_w(int nf, size_t N, DevParams P, const uint32_t *__restrict__ items_f,
            const double *__restrict__ gD, double *__restrict__ lam_s, double *__restrict__ part)
 {
     __shared__ witems::Smem smem[kAdjWarps];
+    __shared__ double slotsm[kAdjWarps][8 * witems::NSLOT];   // balanced-walk partial sums
     const int lane = threadIdx.x & 31;
     witems::Smem &S = smem[threadIdx.x >> 5];
+    double *slots = slotsm[threadIdx.x >> 5];
     const uint32_t nfi = ctr[0];
     const uint32_t n_items = nfi + (use_b ? ctr[3] : 0u);
     for (;;) {
@@ -547,7 +577,7 @@ k_adj_pi_w(int nf, size_t N, DevParams P, const uint32_t *__restrict__ items_f,
         if (it >= n_items) break;
         if (it < nfi)
             adj_fluid_item(P, S, lane, it, nf, N, items_f, posp, velr, posf, cell, fstart, bposp,
-                           bvelr, bposf, bstart, gF, gD, lam_s, part);
+                           bvelr, bposf, bstart, gF, gD, lam_s, part, slots);
         else
             adj_boundary_item(P, S, lane, it - nfi, nf, N, items_b, bposp, bvelr, bposf, bcell,
                               bstart, posp, velr, posf, cell, fstart, gF, lam_s);
