@@ -530,24 +530,36 @@ __device__ __forceinline__ void adj_boundary_item(
     const double4_32a *__restrict__ posp, const double4_32a *__restrict__ velr,
     const float4 *__restrict__ posf, const uint32_t *__restrict__ cell,
     const int32_t *__restrict__ fstart, const double *__restrict__ gF,
-    double *__restrict__ lam_s)
+    double *__restrict__ lam_s, double *slots)
 {
     const witems::Item I = witems::item_of<false>(P, items, it, bcell, bstart, lane);
     const int j = I.i;
-    const double4_32a pb = bposp[j], vb = bvelr[j];
-    const PartTerms tb = part_terms(P, vb.w, pb.w);
     const witems::Frame Fr = witems::frame_of<false>(P, I, bposf[j], bcell);
     const double s2 = 4.0 * P.h * P.h;
-    double lr = 0.0;
-    witems::for_each_hit<false>(P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
-                                [&](int i, bool) {
-        const double4_32a pa = posp[i];
-        const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
-        if (!(rx * rx + ry * ry + rz * rz < s2)) return;
-        const double4_32a va = velr[i];
-        lr += pair_adj_rho_b(P, rx, ry, rz, va.x, va.y, va.z, tb, va.w, sound_of(P, va.w),
-                             gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2]);
-    });
+    // balanced walk: the boundary target this lane works for, its sum (w) and
+    // the total of the lane's own target (lr)
+    int wj = j;
+    double4_32a pb;
+    PartTerms tb;
+    double w = 0.0, lr = 0.0;
+    witems::for_each_hit_balanced<false>(
+        P, S, lane, I, Fr, fstart, posf, bstart, bposf, cell,
+        [&](int t) {
+            wj = I.i0 + t;
+            pb = bposp[wj];
+            tb = part_terms(P, bvelr[wj].w, pb.w);
+            w = 0.0;
+        },
+        [&](int i, bool) {
+            const double4_32a pa = posp[i];
+            const double rx = pa.x - pb.x, ry = pa.y - pb.y, rz = pa.z - pb.z;
+            if (!(rx * rx + ry * ry + rz * rz < s2)) return;
+            const double4_32a va = velr[i];
+            w += pair_adj_rho_b(P, rx, ry, rz, va.x, va.y, va.z, tb, va.w, sound_of(P, va.w),
+                                gF[3 * (size_t)i], gF[3 * (size_t)i + 1], gF[3 * (size_t)i + 2]);
+        },
+        [&](int, int slot) { slots[8 * slot] = w; },
+        [&](int slot) { lr += slots[8 * slot]; });
     if (I.active) lam_s[6 * N + (size_t)nf + j] += lr;
 }
 
@@ -580,7 +592,7 @@ k_adj_pi_w(int nf, size_t N, DevParams P, const uint32_t *__restrict__ items_f,
                            bvelr, bposf, bstart, gF, gD, lam_s, part, slots);
         else
             adj_boundary_item(P, S, lane, it - nfi, nf, N, items_b, bposp, bvelr, bposf, bcell,
-                              bstart, posp, velr, posf, cell, fstart, gF, lam_s);
+                              bstart, posp, velr, posf, cell, fstart, gF, lam_s, slots);
     }
 }
 
