@@ -142,3 +142,51 @@ def test_pi_matches_all_pairs_evaluation(oracle_lib):
     assert np.allclose(ace, ace2, rtol=1e-11, atol=1e-9 * np.abs(ace2).max())
     assert np.allclose(ar, ar2, rtol=1e-11, atol=1e-9 * np.abs(ar2).max())
     assert vm == pytest.approx(vm2, rel=1e-14)
+
+
+def _approaching_pair(v_rel):
+    """Two fluid particles on the x axis, 0.012 m apart, with unequal densities
+    (1000 and 1100 kg/m^3) and so unequal pressures and sound speeds, moving
+    towards each other (v_a = +v_rel/2, v_b = -v_rel/2 along x).  Round
+    constants: h = 0.01 m (support and cell 0.02 m), m = 1e-3 kg, rho0 = 1000,
+    gamma = 7, c0 = 10 m/s, alpha = 0.1, eta^2 = 0.01 h^2, no gravity."""
+    from sphcases.dambreak import RunParams
+    p = RunParams(dp=0.01, h=0.01, cell_size=0.02, c0=10.0, mass=1e-3, g=(0.0, 0.0, 0.0),
+                  dom_min=(0.0, 0.0, 0.0), dom_max=(0.2, 0.2, 0.2))
+    pos = np.array([[0.05, 0.05, 0.05], [0.062, 0.05, 0.05]])
+    vel = np.array([[0.5 * v_rel, 0.0, 0.0], [-0.5 * v_rel, 0.0, 0.0]])
+    rho = np.array([1000.0, 1100.0])
+    return p, pos, vel, rho
+
+
+def test_viscosity_hand_values_unequal_pair(oracle_lib):
+    """Artificial viscosity of Monaghan (1992) (Table 1) on one approaching pair
+    with unequal rho and c, every number worked by hand:
+
+      r_ab = x_a - x_b = (-0.012, 0, 0),  r = 0.012,  q = r/h = 1.2
+      v_ab = (10, 0, 0),  v_ab . r_ab = -0.12  (approaching, so Pi applies)
+      mu_ab = h v.r / (r^2 + eta^2) = 0.01 (-0.12) / (1.44e-4 + 1e-6) = -8.2758620689655
+      c_a = c0 = 10,  c_b = c0 (1.1)^3 = 13.31,  cbar = 11.655,  rhobar = 1050
+      Pi_ab = -alpha cbar mu / rhobar = 0.1 * 11.655 * 8.2758620689655 / 1050 = 9.1862068965517e-3
+      dW/dr (1 <= q < 2) = -0.75 (2 - q)^2 / (pi h^4) = -0.48 / (pi 1e-8),
+      so grad_a W = (1.5278874536822e7, 0, 0)
+      P_a = 0,  P_b / rho_b^2 = (c0^2 rho0 / 7)(1.1^7 - 1) / 1100^2 = 1.1200910271547e-2
+      ace_a = -m (P_b/rho_b^2 + Pi_ab) grad_a W = (-311.49220537886, 0, 0),  ace_b = -ace_a
+      viscous share of ace_a = -m Pi_ab grad_a W = -140.35490264170
+      ar_a = ar_b = m v_ab . grad_a W = 1.5278874536822e5,  max |mu| = 8.2758620689655
+
+    A mu without its factor h, eta^2 taken as 0.01 instead of 0.01 h^2, c_a or
+    c_b in place of cbar, or rho_a or rho_b in place of rhobar each moves
+    Pi_ab (and the viscous share) by 5 % or more."""
+    p, pos, vel, rho = _approaching_pair(10.0)
+    ace, ar, vm, counts, _ = oracle_lib.interact(p, 2, 0, pos, vel, rho)
+    assert ace[0, 0] == pytest.approx(-311.49220537886, rel=1e-11)
+    assert ace[1, 0] == pytest.approx(311.49220537886, rel=1e-11)
+    assert np.abs(ace[:, 1:]).max() == 0.0
+    assert ar == pytest.approx([1.5278874536822e5, 1.5278874536822e5], rel=1e-11)
+    assert vm == pytest.approx(8.2758620689655, rel=1e-11)
+    # receding: no viscosity, the pressure term alone
+    ace_r, ar_r, vm_r, _, _ = oracle_lib.interact(p, 2, 0, pos, -vel, rho)
+    assert ace[0, 0] - ace_r[0, 0] == pytest.approx(-140.35490264170, rel=1e-10)
+    assert ace_r[0, 0] == pytest.approx(-311.49220537886 + 140.35490264170, rel=1e-10)
+    assert vm_r == pytest.approx(8.2758620689655, rel=1e-11)   # |mu| enters dt either way

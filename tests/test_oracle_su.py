@@ -127,3 +127,25 @@ def test_still_tank_stays_hydrostatic(oracle_lib):
         assert abs(got - expect) < 0.05 * expect
     # and the particles are still almost at rest
     assert np.abs(st.vel[:c.n_f]).max() < 0.1
+
+
+def test_time_step_viscous_limit_hand_value(oracle_lib):
+    """dt = CFL min(sqrt(h / max|f|), h / (max c + max|mu|)) (Monaghan & Kos
+    1999, Table 1) where the viscous term binds and matters.  The pair of
+    tests/test_oracle_pi.py (h = 0.01, rho 1000 and 1100, closing at 10 m/s,
+    no gravity) has max c = 13.31, max |mu| = 8.2758620689655 and
+    |f| = 311.49220537886, so by hand
+      force limit:        0.2 sqrt(0.01 / 311.49) = 1.1332e-3
+      sound + viscosity:  0.2 * 0.01 / (13.31 + 8.2758620689655) = 9.2653237272161e-5
+    and dt is the second.  Without the viscous term it would be
+    0.2 * 0.01 / 13.31 = 1.5026e-4."""
+    from tests.test_oracle_pi import _approaching_pair
+    p, pos, vel, rho = _approaching_pair(10.0)
+    ace, ar, vm, counts, _ = oracle_lib.interact(p, 2, 0, pos, vel, rho)
+    dt = oracle_lib.time_step(p, 2, 0, pos, ace, rho, vm)
+    assert dt == pytest.approx(9.2653237272161e-5, rel=1e-11)
+    # the same closing speed ten times lower: |mu| = 0.82758620689655 still adds
+    # 6 % to the sound speed, 0.2 * 0.01 / (13.31 + 0.82758620689655) = 1.4146630e-4
+    ace, ar, vm, counts, _ = oracle_lib.interact(p, 2, 0, pos, 0.1 * vel, rho)
+    dt = oracle_lib.time_step(p, 2, 0, pos, ace, rho, vm)
+    assert dt == pytest.approx(0.2 * 0.01 / (13.31 + 0.82758620689655), rel=1e-11)
