@@ -83,18 +83,3 @@ def test_pi_sampled_targets_5m(torch_mod, O, precision, tol):
     sa = 9.81 + np.abs(oace[fi]).max() if precision == "fp32" else np.abs(oace[fi]).max()
     assert np.abs(ace[fi] - oace[fi]).max() <= tol * sa
     assert np.abs(ar[idx] - oar[idx]).max() <= tol * np.abs(oar[idx]).max()
-
-
-def test_fp32_split_run_1m(torch_mod, O):
-    """20 FP32-split steps of the 1M dam break against 20 oracle steps."""
-    c = dam_break(0.005)
-    sim = make_sim(c, "fp32")
-    st = O.State(c)
-    for _ in range(20):
-        sim.step()
-        st.step()
-    pos, vel, rho = sim.get_state()
-    vscale = np.abs(st.vel).max() + 9.81 * st.time
-    assert np.abs(pos - st.pos).max() <= 1e-4 * c.params.dp
-    assert np.abs(vel - st.vel).max() <= 1e-3 * vscale
-    assert np.abs(rho / st.rho - 1).max() <= 1e-5
