@@ -145,39 +145,67 @@ def test_adjoint_step_needs_fixed_dt_fp64(torch_mod):
             sph.sph_adjoint_step(sim.ctx, lam, lam2, da)
 
 
+CONF4 = dict(steps=400, window=100, dt=1e-4)
+
+
+def _fd_checks(j_of, v0, alpha, gv, ga, alpha_eps, alpha_rel):
+    """Central differences of the forward map j_of(v, alpha) against the
+    adjoint gradient (gv, ga) on the differentiable configuration:
+      * the normalised gradient direction, eps = 1e-3, to 1e-4 relative;
+      * 8 seeded random unit directions d of the initial velocities (N(0, 1)
+        per component, normalised), eps = 1e-3: |FD - g.d| within 1e-4 |g|
+        (|g| bounds |g.d| over unit directions; a random direction's g.d is
+        about |g| / sqrt(n), so the error is stated against the gradient's
+        scale rather than against the cancellation of 241,200 terms);
+      * the 16 components of largest |g|, eps = 1e-5, to 1e-4 relative each
+        (at eps = 1e-3 single components of the wall-pressure objective carry
+        the O(eps) error of pairs crossing the viscosity switch, which is
+        only C0);
+      * alpha at alpha_eps to alpha_rel."""
+    gn = float(np.linalg.norm(gv))
+    d = gv / gn
+    eps = 1e-3
+    fd = (j_of(v0 + eps * d, alpha) - j_of(v0 - eps * d, alpha)) / (2 * eps)
+    assert fd == pytest.approx(gn, rel=1e-4)
+    for s in range(8):
+        d = np.random.default_rng(1000 + s).normal(size=v0.shape)
+        d /= np.linalg.norm(d)
+        fd = (j_of(v0 + eps * d, alpha) - j_of(v0 - eps * d, alpha)) / (2 * eps)
+        assert abs(fd - float((gv * d).sum())) <= 1e-4 * gn, s
+    eps = 1e-5
+    for k in np.argsort(-np.abs(gv).ravel())[:16]:
+        d = np.zeros(v0.size)
+        d[k] = 1.0
+        d = d.reshape(v0.shape)
+        fd = (j_of(v0 + eps * d, alpha) - j_of(v0 - eps * d, alpha)) / (2 * eps)
+        assert fd == pytest.approx(float(gv.ravel()[k]), rel=1e-4), int(k)
+    fd_a = (j_of(v0, alpha + alpha_eps) - j_of(v0, alpha - alpha_eps)) / (2 * alpha_eps)
+    assert fd_a == pytest.approx(ga, rel=alpha_rel)
+
+
 @pytest.mark.slow
 def test_adjoint_differentiable_configuration(torch_mod):
     """dp = 0.01 dam break (80,400 fluid + 58,606 boundary), fixed dt = 1e-4 s,
     400 steps, checkpoints every 20 steps, 64 sensors on the wall behind the
-    column, mean over the last 100 states.  Central differences with eps =
-    1e-3 along the normalised gradient (no cancellation between components)
-    agree to 1e-4 (measured 6.8e-6).  In alpha the sensor objective is rougher:
-    the viscosity switch (Pi = 0 for v.r >= 0) is only C0 and a change of alpha
-    moves many pairs across it, each adding an O(eps) error; at eps = 1e-5 the
-    central difference agrees to 1e-3 (measured 3e-4, 2.5e-3 at eps = 1e-3)."""
+    column, mean over the last 100 states; the checks of _fd_checks.  In
+    alpha the sensor objective is rougher: the viscosity switch (Pi = 0 for
+    v.r >= 0) is only C0 and a change of alpha moves many pairs across it,
+    each adding an O(eps) error; at eps = 1e-5 the central difference agrees
+    to 1e-3 (measured 3e-4, 2.5e-3 at eps = 1e-3)."""
     torch = torch_mod
     c = dam_break(0.01, vel_sigma=0.05, seed=0, fixed_dt=1e-4)
     spos = wall_sensors(c, wall="back")
-    J, gv, ga, run = _gpu_grad(torch, c, spos, k=20, steps=400, window=100, dt=1e-4)
+    J, gv, ga, run = _gpu_grad(torch, c, spos, k=20, **CONF4)
     assert run.stats["checkpoint_bytes"] < 1e9
-    v0 = c.vel[:c.n_f].copy()
-    d = gv / np.linalg.norm(gv)
-    eps = 1e-3
-    fd = (_gpu_j(torch, c, spos, v0 + eps * d, 0.1, steps=400, window=100, dt=1e-4)
-          - _gpu_j(torch, c, spos, v0 - eps * d, 0.1, steps=400, window=100, dt=1e-4)) / (2 * eps)
-    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-4)
-    eps = 1e-5
-    fd_a = (_gpu_j(torch, c, spos, v0, 0.1 + eps, steps=400, window=100, dt=1e-4)
-            - _gpu_j(torch, c, spos, v0, 0.1 - eps, steps=400, window=100, dt=1e-4)) / (2 * eps)
-    assert fd_a == pytest.approx(ga, rel=1e-3)
+    _fd_checks(lambda v, al: _gpu_j(torch, c, spos, v, al, **CONF4), c.vel[:c.n_f].copy(), 0.1,
+               gv, ga, alpha_eps=1e-5, alpha_rel=1e-3)
 
 
 @pytest.mark.slow
 def test_front_objective_differentiable_configuration(torch_mod):
     """The same configuration with the front-position objective (tau = dp, mean
-    over the last 100 states): central differences with eps = 1e-3 along the
-    normalised velocity gradient and in alpha agree to 1e-4 (measured 7e-7 and
-    2.3e-6)."""
+    over the last 100 states): the checks of _fd_checks, alpha at eps = 1e-3
+    to 1e-4 (measured 2.3e-6)."""
     torch = torch_mod
     from paper_1110_3711_gb300.autograd import DamBreakRun, objective
     c = dam_break(0.01, vel_sigma=0.05, seed=0, fixed_dt=1e-4)
@@ -192,10 +220,4 @@ def test_front_objective_differentiable_configuration(torch_mod):
     a = torch.tensor(0.1, dtype=torch.float64, device="cuda", requires_grad=True)
     objective(v0t, a, run).backward()
     gv, ga = v0t.grad.cpu().numpy(), float(a.grad)
-    v0 = c.vel[:c.n_f].copy()
-    d = gv / np.linalg.norm(gv)
-    eps = 1e-3
-    fd = (run_j(v0 + eps * d, 0.1) - run_j(v0 - eps * d, 0.1)) / (2 * eps)
-    assert fd == pytest.approx(np.linalg.norm(gv), rel=1e-4)
-    fd_a = (run_j(v0, 0.1 + eps) - run_j(v0, 0.1 - eps)) / (2 * eps)
-    assert fd_a == pytest.approx(ga, rel=1e-4)
+    _fd_checks(run_j, c.vel[:c.n_f].copy(), 0.1, gv, ga, alpha_eps=1e-3, alpha_rel=1e-4)
