@@ -452,7 +452,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="dam1m")
-    ap.add_argument("--fp64-steps", type=int, default=20)
+    ap.add_argument("--fp64-steps", type=int, default=-1,
+                    help="FP64 steps at the benchmark size (default: the same window as --steps)")
+    ap.add_argument("--late-advance", type=int, default=5000,
+                    help="untimed steps before the late-state timing (0: skip the late state)")
+    ap.add_argument("--late-steps", type=int, default=200)
+    ap.add_argument("--no-20m", action="store_true", help="skip the 21.8M-particle line")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--no-5m", action="store_true", help="skip the 5M-particle lines")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -461,6 +466,8 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if args.fp64_steps < 0:
+        args.fp64_steps = args.steps
     world, rank, local = dist_env()
 
     if args.impl == "reference":
@@ -493,7 +500,9 @@ def main():
     del sim
     r64 = None
     if args.fp64_steps > 0:
-        sim64, r64 = run_form(torch, case, "fp64", args.fp64_steps, 3, flush, world)
+        # same warm-up as the FP32 run, so that with fp64_steps == steps both
+        # forms are timed over the same window of the flow
+        sim64, r64 = run_form(torch, case, "fp64", args.fp64_steps, args.warmup, flush, world)
         del sim64
 
     extra = {}
@@ -519,25 +528,61 @@ def main():
                            "candidates_per_step": r64["counts"][0] + r64["counts"][2]}
             for name, kname, cs in (("fp64_thread", "thread", case),
                                     ("fp64_hcells", "warp", fine)):
-                s_a, r_a = run_form(torch, cs, "fp64", args.fp64_steps, 3, flush, world,
+                s_a, r_a = run_form(torch, cs, "fp64", min(args.fp64_steps, 50), 3, flush, world,
                                     pi_kernel=kname)
                 del s_a
                 abl[name] = {"steps_per_s": r_a["steps_per_s"], "pi_ms": r_a["pi_ms"],
                              "candidates_per_step": r_a["counts"][0] + r_a["counts"][2]}
         extra["pi_kernel_ablation"] = abl
+    if args.late_advance > 0 and args.late_steps > 0:
+        # the same workload after the column has collapsed: the untimed
+        # advance runs as the warm-up, then steps are timed as above
+        s_l, r_l = run_form(torch, case, "fp32", args.late_steps, args.late_advance, flush, world)
+        del s_l
+        fl = pi_flops(r_l["counts"])
+        ach = fl / (r_l["pi_ms"] / 1e3) / 1e12
+        extra["late_state"] = {
+            "advance_steps": args.late_advance, "steps": args.late_steps,
+            "sim_time_s": r_l["sim_time_s"], "steps_per_s": r_l["steps_per_s"],
+            "ms_per_step": r_l["ms_per_step"], "interactions_per_s": r_l["interactions_per_s"],
+            "stage_ms": r_l["stage_ms"], "counts": r_l["counts"],
+            "roofline": {"bound": "alu", "achieved": ach, "peak": fp32_peak_tflops(),
+                         "unit": "TFLOP/s", "frac": ach / fp32_peak_tflops(),
+                         "flops_per_call": fl},
+            "status_flags": r_l["status_flags"]}
     if not args.no_5m and args.workload != "dam5m":
         case5 = dam_break(WORKLOADS["dam5m"]["dp"])
-        s5, r5 = run_form(torch, case5, "fp32", 100, 5, flush, world)
+        n5 = 100
+        s5, r5 = run_form(torch, case5, "fp32", n5, 5, flush, world)
         del s5
-        s5d, r5d = run_form(torch, case5, "fp64", 5, 3, flush, world)
+        s5d, r5d = run_form(torch, case5, "fp64", n5, 5, flush, world)
         del s5d
-        extra["dam5m"] = {"particles": case5.n, "fp32_steps_per_s": r5["steps_per_s"],
+        extra["dam5m"] = {"particles": case5.n, "steps": n5, "warmup": 5,
+                          "fp32_steps_per_s": r5["steps_per_s"],
                           "fp32_interactions_per_s": r5["interactions_per_s"],
                           "fp32_stage_ms": r5["stage_ms"],
                           "fp64_steps_per_s": r5d["steps_per_s"],
                           "fp64_interactions_per_s": r5d["interactions_per_s"],
-                          "fp32_over_fp64": r5["steps_per_s"] / r5d["steps_per_s"]}
+                          "fp64_stage_ms": r5d["stage_ms"],
+                          "fp32_over_fp64": r5["steps_per_s"] / r5d["steps_per_s"],
+                          "window": "both forms timed over the same steps 6-105 from rest"}
         del case5
+    if not args.no_20m and args.workload != "dam20m":
+        # configuration of the large dam break: 500 steps, NL / PI / SU shares
+        case20 = dam_break(WORKLOADS["dam20m"]["dp"])
+        s20, r20 = run_form(torch, case20, "fp32", 500, 5, flush, world)
+        del s20
+        st_ms = r20["stage_ms"]
+        tot_ms = sum(st_ms.values())
+        fl = pi_flops(r20["counts"])
+        extra["dam20m"] = {"particles": case20.n, "steps": 500, "warmup": 5,
+                           "steps_per_s": r20["steps_per_s"],
+                           "interactions_per_s": r20["interactions_per_s"],
+                           "stage_ms": st_ms,
+                           "stage_share": {k: v / tot_ms for k, v in st_ms.items()},
+                           "pi_roofline_frac": fl / (r20["pi_ms"] / 1e3) / 1e12 / fp32_peak_tflops(),
+                           "sim_time_s": r20["sim_time_s"], "status_flags": r20["status_flags"]}
+        del case20
 
     pk = peaks()
     fma = measured_fma(torch)

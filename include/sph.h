@@ -298,9 +298,10 @@ int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *lam, double *
  * Every output is device memory the caller owns.  The same outputs as the fluid
  * part of sph_neighbour_list for the same positions, bit for bit.
  * Scratch: one fixed device array inside the library (about 8.7 MB), held by
- * every GPU that loads the library until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture.
+ * every GPU that loads the library until the process exits.  Every call looks
+ * up that array's device address on the current device (cudaGetSymbolAddress);
+ * the first call on a device may also load the library's device code there, so
+ * make that first call before any stream capture.
  * Every call shares the array and leaves its contents behind, so calls that
  * overlap on the GPU (other streams, other host threads) race: serialise them. */
 int sph_neighbour_list_static(const sph_params *p, int64_t n, const double *pos,

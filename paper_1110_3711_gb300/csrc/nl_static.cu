@@ -11,9 +11,11 @@
 //
 // In host code the name g_nl_scratch is only a stand-in for the device
 // symbol, not a device address: a kernel given it would fault (or silently
-// touch host memory where the GPU can reach it).  The first call on each
-// device therefore looks up the real address with cudaGetSymbolAddress, with
-// that device current, and caches it; kernels are given that address.
+// touch host memory where the GPU can reach it).  Every call therefore looks
+// up the real address with cudaGetSymbolAddress, with the caller's device
+// current, and gives kernels that address.  The lookup is not cached: a cached
+// address would outlive a cudaDeviceReset or a new primary context, and the
+// lookup costs little next to the sort.
 //
 // The work is the same as the fluid part of sph_neighbour_list (cell of each
 // point, stable radix sort by (cell, id), first index of every cell) and uses
@@ -21,8 +23,6 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
-
-#include <mutex>
 
 #include "sph_internal.cuh"
 
@@ -38,27 +38,14 @@ constexpr int64_t kScanMax = kHistWords > kMaxCells + 2 ? kHistWords : kMaxCells
 constexpr int64_t kPartWords = (kScanMax + kScanTile - 1) / kScanTile + 1;
 // key and value in id order, key and value ping-pong, histograms, partials
 constexpr int64_t kScratchWords = 4 * kMaxPoints + kHistWords + kPartWords;
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) uint32_t g_nl_scratch[kScratchWords];
 
-std::mutex g_mutex;
-uint32_t *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of g_nl_scratch on the current device (looked up once per
-// device, with that device current).
+// Device address of g_nl_scratch on the current device.
 int scratch_address(uint32_t **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return SPH_ERR_CUDA;
-    if (dev < 0 || dev >= kMaxDevices) return SPH_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> lock(g_mutex);
-    if (!g_scratch_addr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_nl_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
-        g_scratch_addr[dev] = (uint32_t *)p;
-    }
-    *out = g_scratch_addr[dev];
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_nl_scratch) != cudaSuccess || !p) return SPH_ERR_CUDA;
+    *out = (uint32_t *)p;
     return SPH_OK;
 }
 

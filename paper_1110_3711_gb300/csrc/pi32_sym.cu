@@ -41,6 +41,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pair32.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
@@ -67,20 +68,6 @@ struct WarpSmem {
     int code[NRUN];       // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4), own row (bit 5)
 };
 
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
 __device__ __forceinline__ void red_add_v4(float4 *p, float a, float b, float c, float d)
 {
     asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b),
@@ -96,18 +83,9 @@ __device__ __forceinline__ void pair_sym(const DevParams &P, float rx, float ry,
                                          float pra, const float4 &va, float cpa, const float4 &vb,
                                          float prb, float &coef, float &cF, float &vis)
 {
-    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
-    const float q = r2 * rinv;
-    const float t = 2.0f - q;
-    const float F = q < 1.0f ? fmaf(P.gw1, q, P.gw0) : t * t * rinv;
-    const float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
-    const float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
-    const float mu = vdr * rcp_approx(r2 + P.eta2_h2f);
-    const float cc = fmaf(P.kcf, vb.w * vb.w * vb.w, cpa);
-    coef = fmaf(cc * fminf(mu, 0.0f), rcp_approx(va.w + vb.w), pra + prb) * F;
+    float vdr, F;
+    pair_terms32<true, false>(P, rx, ry, rz, pra, va, cpa, vb, prb, coef, vdr, F, vis);
     cF = vdr * F;
-    vis = fmaxf(vis, fabsf(mu));
 }
 
 __global__ void __launch_bounds__(WARPS * 32)

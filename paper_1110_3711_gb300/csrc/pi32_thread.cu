@@ -14,62 +14,22 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "pair32.cuh"
 #include "sph_internal.cuh"
 
 namespace sph {
 
 namespace {
 
-struct AccT {
-    float ax, ay, az, ar, vis;
-};
-
-__device__ __forceinline__ float rcp_approx(float x)
-{
-    float y;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-__device__ __forceinline__ float rsqrt_approx(float x)
-{
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Pair terms with the arithmetic of the warp kernel (pi32.cu), in units of h:
-// r' = r / h, q = |r'|, F'' = (kA h / kB)(2.25 q - 3) for q < 1 and
-// (2 - q)^2 / q otherwise, mu = v.r' / (q^2 + eta^2/h^2), -alpha c_b =
-// (-alpha c0 / rho0^3) rho_b^3; the sums hold (P_a/rho_a^2 + P_b/rho_b^2 + Pi)
-// F'' r' and (v.r') F'', and the factors -m kB and m kB are applied once per
-// target.  cpa = -alpha c_a; r_ab comes in metres.
+// The pair terms of the warp kernel (pair32.cuh, units of h) for r_ab in
+// metres; cpa = -alpha c_a.
 template <bool MOMENTUM>
 __device__ __forceinline__ void pair_t(const DevParams &P, const float4 &pa, const float4 &va,
                                        float cpa, const float4 &pb, const float4 &vb, float rx,
-                                       float ry, float rz, AccT &o)
+                                       float ry, float rz, Acc32 &o)
 {
-    rx *= P.invhf;
-    ry *= P.invhf;
-    rz *= P.invhf;
-    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
-    const float q = r2 * rinv;
-    const float t = 2.0f - q;
-    const float F = q < 1.0f ? fmaf(P.gw1, q, P.gw0) : t * t * rinv;
-    const float dvx = va.x - vb.x, dvy = va.y - vb.y, dvz = va.z - vb.z;
-    const float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
-    const float mu = vdr * rcp_approx(r2 + P.eta2_h2f);
-    if (MOMENTUM) {
-        const float cc = fmaf(P.kcf, vb.w * vb.w * vb.w, cpa);
-        const float coef =
-            fmaf(cc * fminf(mu, 0.0f), rcp_approx(va.w + vb.w), pa.w + pb.w) * F;
-        o.ax = fmaf(coef, rx, o.ax);
-        o.ay = fmaf(coef, ry, o.ay);
-        o.az = fmaf(coef, rz, o.az);
-    }
-    o.ar = fmaf(vdr, F, o.ar);
-    o.vis = fmaxf(o.vis, fabsf(mu));
+    pair_acc32<MOMENTUM, false>(P, rx * P.invhf, ry * P.invhf, rz * P.invhf, pa.w, va, cpa, vb,
+                                pb.w, o);
 }
 
 // Candidates of one x-run: each gets the shift of its own cell x + k
@@ -79,7 +39,7 @@ template <bool MOMENTUM, int R>
 __device__ __forceinline__ void walk_range(const DevParams &P, const float4 &pa, const float4 &va,
                                            float ca, int j0, int j1, const int (&cut)[2 * R],
                                            int dy, int dz, const float4 *__restrict__ posp,
-                                           const float4 *__restrict__ velr, AccT &o)
+                                           const float4 *__restrict__ velr, Acc32 &o)
 {
     const float ya = pa.y - (float)dy * P.sf;
     const float za = pa.z - (float)dz * P.sf;
@@ -106,7 +66,7 @@ __device__ __forceinline__ void runs_t(const DevParams &P, const float4 &pa, con
                                        const float4 *__restrict__ posp,
                                        const float4 *__restrict__ velr,
                                        const int32_t *__restrict__ start,
-                                       const int4 *__restrict__ ranges, AccT &o)
+                                       const int4 *__restrict__ ranges, Acc32 &o)
 {
     constexpr int W = 2 * R + 1;
     for (int q = 0; q < W * W; ++q) {
@@ -153,7 +113,7 @@ k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
                   cz = (int)(t / (uint32_t)P.ny);
         const float ra = va.w * P.inv_rho0f;
         const float ca = P.nalphaf * (P.c0f * ra * ra * ra);  // -alpha c_a
-        AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
+        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, posp, velr, fstart, franges, o);
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, bposp, bvelr, bstart, branges, o);
         const float ax = fmaf(P.nmkBf, o.ax, P.gf[0]);
@@ -186,7 +146,7 @@ k_pi_thread_boundary(int nb, DevParams P, const float4 *__restrict__ bposp,
         const uint32_t t = c / (uint32_t)P.nx;
         const int cx = (int)(c - t * (uint32_t)P.nx), cy = (int)(t % (uint32_t)P.ny),
                   cz = (int)(t / (uint32_t)P.ny);
-        AccT o = {0.f, 0.f, 0.f, 0.f, 0.f};
+        Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
         runs_t<false, FAST, R>(P, pa, va, 0.f, c, cx, cy, cz, posp, velr, fstart, franges, o);
         bar[i] = P.mkBf * o.ar;
         vis = (double)o.vis;

@@ -9,6 +9,7 @@ arrays are float64 in persistent-id order, fluid first.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import threading
 
@@ -313,11 +314,40 @@ STATIC_MAX_POINTS = 524288
 STATIC_MAX_CELLS = 16777216
 
 
+def static_grid_cells(p: sph_params) -> int:
+    """Number of cells of the grid that sph_neighbour_list_static builds for p
+    (ceil(span / cell_size) per axis), i.e. cell_start holds this + 2 entries."""
+    n = 1
+    for d in range(3):
+        n *= int(math.ceil((p.dom_max[d] - p.dom_min[d]) / p.cell_size))
+    return n
+
+
 def sph_neighbour_list_static(p: sph_params, n, pos, sorted_id, cell, cell_start, stream=None):
     """Neighbour list of n points with no device allocation (see include/sph.h):
-    pos and the three outputs are device arrays the caller owns."""
-    _check(lib().sph_neighbour_list_static(C.byref(p), int(n), _ptr(pos), _ptr(sorted_id),
-                                           _ptr(cell), _ptr(cell_start), stream),
+    pos and the three outputs are CUDA tensors the caller owns, of exactly
+    the sizes the call reads and writes (float64 [n][3]; 32-bit [n], [n];
+    int32 [n_cells + 2])."""
+    import torch
+    n = int(n)
+    if n < 0:
+        raise ValueError("n must be >= 0")
+    bufs = {"pos": pos, "sorted_id": sorted_id, "cell": cell, "cell_start": cell_start}
+    for name, t in bufs.items():
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+    if pos.dtype != torch.float64:
+        raise TypeError(f"pos must be float64, got {pos.dtype}")
+    u32 = (torch.int32,) + ((torch.uint32,) if hasattr(torch, "uint32") else ())
+    for name in ("sorted_id", "cell"):
+        if bufs[name].dtype not in u32:
+            raise TypeError(f"{name} must be a 32-bit integer tensor, got {bufs[name].dtype}")
+    if cell_start.dtype != torch.int32:
+        raise TypeError(f"cell_start must be int32, got {cell_start.dtype}")
+    ncells = static_grid_cells(p)
+    _check(lib().sph_neighbour_list_static(C.byref(p), n, _ptr(pos, np.float64, 3 * n),
+                                           _ptr(sorted_id, np.uint32, n), _ptr(cell, np.uint32, n),
+                                           _ptr(cell_start, np.int32, ncells + 2), stream),
            "sph_neighbour_list_static")
 
 
