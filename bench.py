@@ -305,24 +305,31 @@ def e2e_form(torch, sim, steps):
                 note="state uploaded from and read back to pinned host memory every step")
 
 
-def code_hash(path):
-    """sha256 (16 hex digits) of a C/CUDA source with its comments and
+def code_hash(paths):
+    """sha256 (16 hex digits) of C/CUDA sources with their comments and
     whitespace removed: edits of comments do not change it, edits of code do."""
     import re
-    src = open(path, encoding="utf-8").read()
-    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    src = re.sub(r"//[^\n]*", "", src)
-    src = re.sub(r"\s+", "", src)
+    src = ""
+    for path in paths:
+        s = open(path, encoding="utf-8").read()
+        s = re.sub(r"/\*.*?\*/", "", s, flags=re.S)
+        s = re.sub(r"//[^\n]*", "", s)
+        src += re.sub(r"\s+", "", s)
     return hashlib.sha256(src.encode()).hexdigest()[:16]
 
 
-def traffic_from_profiles(kernel_src):
+# the sources of the FP32 PI kernel k_pi32
+PI32_SOURCES = [os.path.join(ROOT, "paper_1110_3711_gb300", "csrc", f)
+                for f in ("pi32.cu", "warp_items.cuh", "pair32.cuh")]
+
+
+def traffic_from_profiles(kernel_srcs):
     """DRAM bytes per PI call from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    the current kernel sources; else None."""
     path = os.path.join(ROOT, "profiles", "pi_dram_traffic.txt")
     if not os.path.exists(path):
         return None
-    sha = code_hash(kernel_src)
+    sha = code_hash(kernel_srcs)
     vals = {}
     for ln in open(path):
         if "=" in ln and not ln.startswith("#"):
@@ -590,7 +597,7 @@ def main():
     flops = pi_flops(r32["counts"])
     achieved = flops / (r32["pi_ms"] / 1e3) / 1e12
     peak = fp32_peak_tflops()
-    traffic = traffic_from_profiles(os.path.join(ROOT, "paper_1110_3711_gb300", "csrc", "pi32.cu"))
+    traffic = traffic_from_profiles(PI32_SOURCES)
 
     g = r32.get("graph")
     sps = g["steps_per_s"] if g else r32["steps_per_s"]

@@ -456,7 +456,7 @@ __device__ __forceinline__ void adj_fluid_item(
 {
     const witems::Item I = witems::item_of<true>(P, items, it, cell, fstart, lane);
     const int i = I.i;
-    const witems::Frame Fr = witems::frame_of<true>(P, I, posf[i], cell);
+    const witems::Frame Fr = witems::frame_of<true>(P, I, posf[i], cell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // the target this lane works for in the balanced walk, its sums (w), and
     // the total of the lane's own target (l)
@@ -534,7 +534,7 @@ __device__ __forceinline__ void adj_boundary_item(
 {
     const witems::Item I = witems::item_of<false>(P, items, it, bcell, bstart, lane);
     const int j = I.i;
-    const witems::Frame Fr = witems::frame_of<false>(P, I, bposf[j], bcell);
+    const witems::Frame Fr = witems::frame_of<false>(P, I, bposf[j], bcell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // balanced walk: the boundary target this lane works for, its sum (w) and
     // the total of the lane's own target (lr)
@@ -651,7 +651,7 @@ __device__ __forceinline__ int sensor_axis(double x, double mn, double inv_s, in
 template <typename Real>
 __global__ void k_sensor(int S, DevParams P, const double *__restrict__ spos,
                          const double *__restrict__ x, const double *__restrict__ y,
-                         const double *__restrict__ z, const Real *__restrict__ rho,
+                         const double *__restrict__ z, const typename Real4T<Real>::T *__restrict__ V,
                          const int32_t *__restrict__ fstart, double *__restrict__ p_out,
                          double *__restrict__ den_out)
 {
@@ -679,7 +679,7 @@ __global__ void k_sensor(int S, DevParams P, const double *__restrict__ spos,
                     double dx = xs - x[b], dy2 = ys - y[b], dz2 = zs - z[b];
                     double r2 = dx * dx + dy2 * dy2 + dz2 * dz2;
                     if (r2 < s2) {
-                        double rb = (double)rho[b];
+                        double rb = (double)V[b].w;
                         double w = kernel_w(P, sqrt(r2)) * P.mass / rb;
                         num += w * pressure_of(P, rb);
                         den += w;
@@ -706,12 +706,12 @@ __global__ void k_sensor_adj(int nf, size_t N, int S, DevParams P, const double 
                              const double *__restrict__ g, const double *__restrict__ ps,
                              const double *__restrict__ dens, const double *__restrict__ x,
                              const double *__restrict__ y, const double *__restrict__ z,
-                             const double *__restrict__ rho, const uint32_t *__restrict__ id,
+                             const double4_32a *__restrict__ V, const uint32_t *__restrict__ id,
                              const int32_t *__restrict__ fstart, double *__restrict__ lam)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf || i >= fstart[P.ncells]) return;
-    const double xi = x[i], yi = y[i], zi = z[i], rb = rho[i];
+    const double xi = x[i], yi = y[i], zi = z[i], rb = V[i].w;
     const double Pb = pressure_of(P, rb), cb = sound_of(P, rb);
     const double s2 = 4.0 * P.h * P.h;
     double lx = 0, ly = 0, lz = 0, lr = 0;
@@ -746,7 +746,8 @@ int sensor_launch(sph_ctx *ctx, const double *spos, int S, double *p_out, double
     const int c = ctx->cur;
     const int T = 128;
     SPH_LAUNCH(ctx, k_sensor<Real>, (S * 32 + T - 1) / T, T, 0, ctx->stream, S, ctx->dp, spos,
-               w.x[c], w.y[c], w.z[c], (const Real *)w.rho[c], w.fstart, p_out, den_out);
+               w.x[c], w.y[c], w.z[c], (const typename Real4T<Real>::T *)w.V[c], w.fstart, p_out,
+               den_out);
     return check_cuda(cudaGetLastError());
 }
 
@@ -835,7 +836,7 @@ extern "C" int sph_sensor_adjoint(sph_ctx *ctx, const double *sensors, int64_t n
     const int T = 128;
     SPH_LAUNCH(ctx, k_sensor_adj, (nf + T - 1) / T, T, 0, ctx->stream, nf, N, (int)n_sensors,
                ctx->dp, sensors, dj_dp, w.sens_p, w.sens_den, w.x[c], w.y[c], w.z[c],
-               (const double *)w.rho[c], w.id[c], w.fstart, lam);
+               (const double4_32a *)w.V[c], w.id[c], w.fstart, lam);
     return check_cuda(cudaGetLastError());
 }
 
@@ -884,20 +885,20 @@ extern "C" int sph_adjoint_step(sph_ctx *ctx, const double *lam_next, double *la
         if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, sizeof(uint32_t), st))) return SPH_ERR_CUDA;
         SPH_LAUNCH(ctx, k_adj_pi_w, ctx->adj_grid, kAdjWarps * 32, 0, st, nf, N, ctx->dp,
                    w.items_f, w.items_b, w.ctr, nb > 0 ? 1 : 0, &w.ctr[1],
-                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.posf, w.cell,
+                   (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx), w.posf, w.cell,
                    w.fstart, (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bposf,
                    w.bcell, w.bstart, w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part);
         nparts = nf;
     } else {
         if (nf > 0)
             SPH_LAUNCH(ctx, k_adj_pi_fluid, blocks_f, T, 0, st, nf, N, ctx->dp,
-                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
+                       (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx), w.cell, w.fstart,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
                        w.adj_gF, w.adj_gD, w.adj_lam, w.adj_part, w.posf, w.bposf);
         if (nb > 0 && nf > 0)
             SPH_LAUNCH(ctx, k_adj_pi_boundary, (nb + T - 1) / T, T, 0, st, nf, nb, N, ctx->dp,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell,
-                       w.bstart, (const double4_32a *)w.posp, (const double4_32a *)w.velr,
+                       w.bstart, (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx),
                        w.fstart, w.adj_gF, w.adj_gD, w.adj_lam, w.posf, w.bposf);
     }
     if (N > 0)

@@ -177,16 +177,14 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
         W.x[k] = b.take<double>(nf);
         W.y[k] = b.take<double>(nf);
         W.z[k] = b.take<double>(nf);
-        void **arrs[8] = {&W.vx[k], &W.vy[k], &W.vz[k], &W.vmx[k], &W.vmy[k], &W.vmz[k],
-                          &W.rho[k], &W.rhom[k]};
-        for (int a = 0; a < 8; ++a) *arrs[a] = b.take<char>(R * nf);
+        W.V[k] = b.take<char>(V4 * nf);
+        W.VM[k] = b.take<char>(V4 * nf);
         W.id[k] = b.take<uint32_t>(nf);
         b.off = (b.off + 255) & ~(size_t)255;
         W.state_chunk[k] = base ? base + start : nullptr;
         W.state_chunk_bytes = b.off - start;
     }
     W.posp = b.take<char>(V4 * nf);
-    W.velr = b.take<char>(V4 * nf);
     W.acc = b.take<char>(V4 * nf);
     W.cell = b.take<uint32_t>(nf);
     {
@@ -216,8 +214,10 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.val_tmp = b.take<uint32_t>(m);
     W.key_sorted = b.take<uint32_t>(m);
     W.val_sorted = b.take<uint32_t>(m);
-    W.count = b.take<uint32_t>((size_t)*ncells + 2 + kCtrWords);
-    W.ctr = W.count ? W.count + *ncells + 2 : nullptr;
+    const size_t ftiles = (size_t)scan_tiles((int64_t)*ncells + 2);
+    W.count = b.take<uint32_t>((size_t)*ncells + 2 + ftiles + kCtrWords);
+    W.fpart = W.count ? W.count + *ncells + 2 : nullptr;
+    W.ctr = W.count ? W.fpart + ftiles : nullptr;
     W.items_f = b.take<uint32_t>(nf > 0 ? nf : 1);
     W.items_b = b.take<uint32_t>(2 * (size_t)(nb > 0 ? nb : 1));  // {first, count} pairs
     if (p.precision == SPH_FP32_SPLIT && p.pi_kernel == SPH_PI_THREAD_FASTCELLS) {
@@ -250,8 +250,8 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
 
 template <typename Real>
 __global__ void k_scatter_in(int nf, size_t N, const double *__restrict__ stage, double *x,
-                             double *y, double *z, Real *vx, Real *vy, Real *vz, Real *vmx,
-                             Real *vmy, Real *vmz, Real *rho, Real *rhom, uint32_t *id)
+                             double *y, double *z, typename Real4T<Real>::T *V,
+                             typename Real4T<Real>::T *VM, uint32_t *id)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nf) return;
@@ -260,36 +260,39 @@ __global__ void k_scatter_in(int nf, size_t N, const double *__restrict__ stage,
     x[i] = pos[3 * (size_t)i];
     y[i] = pos[3 * (size_t)i + 1];
     z[i] = pos[3 * (size_t)i + 2];
-    vx[i] = (Real)vel[3 * (size_t)i];
-    vy[i] = (Real)vel[3 * (size_t)i + 1];
-    vz[i] = (Real)vel[3 * (size_t)i + 2];
-    vmx[i] = (Real)vm[3 * (size_t)i];
-    vmy[i] = (Real)vm[3 * (size_t)i + 1];
-    vmz[i] = (Real)vm[3 * (size_t)i + 2];
-    rho[i] = (Real)r[i];
-    rhom[i] = (Real)rm[i];
+    typename Real4T<Real>::T v, u;
+    v.x = (Real)vel[3 * (size_t)i];
+    v.y = (Real)vel[3 * (size_t)i + 1];
+    v.z = (Real)vel[3 * (size_t)i + 2];
+    v.w = (Real)r[i];
+    u.x = (Real)vm[3 * (size_t)i];
+    u.y = (Real)vm[3 * (size_t)i + 1];
+    u.z = (Real)vm[3 * (size_t)i + 2];
+    u.w = (Real)rm[i];
+    V[i] = v;
+    VM[i] = u;
     id[i] = (uint32_t)i;
 }
 
 template <typename Real>
 __global__ void k_gather_out(int nf, int nb, size_t N, double *__restrict__ stage,
-                             const double *x, const double *y, const double *z, const Real *vx,
-                             const Real *vy, const Real *vz, const Real *vmx, const Real *vmy,
-                             const Real *vmz, const Real *rho, const Real *rhom,
-                             const uint32_t *id, const double *bx, const double *by,
-                             const double *bz, const Real *brho, const Real *brhom,
-                             const uint32_t *bid)
+                             const double *x, const double *y, const double *z,
+                             const typename Real4T<Real>::T *V,
+                             const typename Real4T<Real>::T *VM, const uint32_t *id,
+                             const double *bx, const double *by, const double *bz,
+                             const Real *brho, const Real *brhom, const uint32_t *bid)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     double *pos = stage, *vel = stage + 3 * N, *r = stage + 6 * N, *vm = stage + 7 * N,
            *rm = stage + 10 * N;
     if (i < nf) {
         size_t k = id[i];
+        const typename Real4T<Real>::T v = V[i], u = VM[i];
         pos[3 * k] = x[i]; pos[3 * k + 1] = y[i]; pos[3 * k + 2] = z[i];
-        vel[3 * k] = (double)vx[i]; vel[3 * k + 1] = (double)vy[i]; vel[3 * k + 2] = (double)vz[i];
-        vm[3 * k] = (double)vmx[i]; vm[3 * k + 1] = (double)vmy[i]; vm[3 * k + 2] = (double)vmz[i];
-        r[k] = (double)rho[i];
-        rm[k] = (double)rhom[i];
+        vel[3 * k] = (double)v.x; vel[3 * k + 1] = (double)v.y; vel[3 * k + 2] = (double)v.z;
+        vm[3 * k] = (double)u.x; vm[3 * k + 1] = (double)u.y; vm[3 * k + 2] = (double)u.z;
+        r[k] = (double)v.w;
+        rm[k] = (double)u.w;
     } else if (i < nf + nb) {
         int j = i - nf;
         size_t k = bid[j];
@@ -364,9 +367,8 @@ template <typename Real> void launch_scatter_in(sph_ctx *ctx, int buf)
     size_t N = (size_t)(ctx->nf + ctx->nb);
     const int T = 256;
     SPH_LAUNCH(ctx, k_scatter_in<Real>, (nf + T - 1) / T, T, 0, ctx->stream, nf, N, w.stage,
-               w.x[buf], w.y[buf], w.z[buf], (Real *)w.vx[buf], (Real *)w.vy[buf],
-               (Real *)w.vz[buf], (Real *)w.vmx[buf], (Real *)w.vmy[buf], (Real *)w.vmz[buf],
-               (Real *)w.rho[buf], (Real *)w.rhom[buf], w.id[buf]);
+               w.x[buf], w.y[buf], w.z[buf], (typename Real4T<Real>::T *)w.V[buf],
+               (typename Real4T<Real>::T *)w.VM[buf], w.id[buf]);
 }
 
 template <typename Real> void launch_gather_out(sph_ctx *ctx)
@@ -378,10 +380,9 @@ template <typename Real> void launch_gather_out(sph_ctx *ctx)
     if (N == 0) return;
     const int T = 256;
     SPH_LAUNCH(ctx, k_gather_out<Real>, (unsigned)((N + T - 1) / T), T, 0, ctx->stream, nf, nb,
-               N, w.stage, w.x[c], w.y[c], w.z[c], (const Real *)w.vx[c], (const Real *)w.vy[c],
-               (const Real *)w.vz[c], (const Real *)w.vmx[c], (const Real *)w.vmy[c],
-               (const Real *)w.vmz[c], (const Real *)w.rho[c], (const Real *)w.rhom[c], w.id[c],
-               w.bx, w.by, w.bz, (const Real *)w.brho, (const Real *)w.brhom, w.bid);
+               N, w.stage, w.x[c], w.y[c], w.z[c], (const typename Real4T<Real>::T *)w.V[c],
+               (const typename Real4T<Real>::T *)w.VM[c], w.id[c], w.bx, w.by, w.bz,
+               (const Real *)w.brho, (const Real *)w.brhom, w.bid);
 }
 
 // Copy the caller's id-ordered state into the stage; missing previous levels

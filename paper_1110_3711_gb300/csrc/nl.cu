@@ -3,15 +3,19 @@
 // Fluid (every step), a counting sort by cell:
 //   k_hash        cell of every particle: c_d = floor((x_d - min_d) / s), linear
 //                 id cx + nx (cy + ny cz) (cells follow X, Y, Z; Section 4.4),
-//                 the per-cell counts and a slot inside the cell (atomics).
+//                 the per-cell counts and a slot inside the cell (atomics),
+//                 and the counts per scan tile of kScanTile cells.
 //   cell starts   exclusive scan of the per-cell counts: start[c] = number of
 //                 particles in cells below c, i.e. CellBeginEnd of Fig. 8 with
-//                 empty cells as equal begin and end.
+//                 empty cells as equal begin and end; its tile sums come from
+//                 k_hash, so the scan is one down-sweep kernel.
 //   k_place       cell-grouped order start[c] + slot (arbitrary inside a cell).
 //   k_reorder     rank by id inside the cell, which gives the (cell, id) order
-//                 whatever the order before; copy of every fluid array to that
-//                 place, plus the packed PI inputs of Section 4.3 {pos, P/rho^2},
-//                 {vel, rho} and the largest sound speed (Section 4.1 maxima).
+//                 whatever the order before; copy of the fluid state (x, y, z
+//                 and the {v, rho} records of both levels) to that place, the
+//                 packed PI input {pos, P/rho^2} of Section 4.3 (the other
+//                 one, {v, rho}, is the state record itself) and the largest
+//                 sound speed (Section 4.1 maxima).
 // Boundary (once) and the static entry point: a stable LSD radix sort of the
 // keys in id order, 8-bit digits: k_radix_hist (tile histograms), exclusive
 // scan (digit-major), k_radix_scatter (ranks from warp match + per-warp digit
@@ -92,7 +96,8 @@ __device__ __forceinline__ uint32_t cell_of(const DevParams &P, double x, double
 __global__ void k_hash(const double *__restrict__ x, const double *__restrict__ y,
                        const double *__restrict__ z, int n, DevParams P,
                        uint32_t *__restrict__ cell_i, uint32_t *__restrict__ slot_i,
-                       uint32_t *__restrict__ count, Scalars *sc)
+                       uint32_t *__restrict__ count, uint32_t *__restrict__ tile_count,
+                       Scalars *sc)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
@@ -103,6 +108,11 @@ __global__ void k_hash(const double *__restrict__ x, const double *__restrict__ 
     uint32_t base = 0;
     if (i < n && lane == leader) base = atomicAdd(&count[c], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
+    // the same count per scan tile of kScanTile cells (the tile sums of the
+    // cell-start scan, so that it needs only its down-sweep)
+    const uint32_t tile = i < n ? c / (uint32_t)kScanTile : 0xffffffffu;
+    const unsigned tpeers = __match_any_sync(0xffffffffu, tile);
+    if (i < n && lane == __ffs(tpeers) - 1) atomicAdd(&tile_count[tile], (uint32_t)__popc(tpeers));
     if (i < n) {
         cell_i[i] = c;
         slot_i[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
@@ -299,6 +309,15 @@ k_scan_down(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *__rest
 
 size_t scan_partials(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
 
+int exclusive_scan_down_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                            const uint32_t *partials, cudaStream_t st)
+{
+    if (n <= 0) return SPH_OK;
+    const int64_t blocks = scan_tiles(n);
+    SPH_LAUNCH(ctx, k_scan_down, (unsigned)blocks, kScanBlock, 0, st, in, out, n, partials);
+    return check_cuda(cudaGetLastError());
+}
+
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *partials, cudaStream_t st)
 {
@@ -339,9 +358,7 @@ int radix_sort(sph_ctx *ctx, const uint32_t *kin, const uint32_t *vin, uint32_t 
 
 // ---------------------------------------------------------------- reorder --
 
-template <typename Real> struct Vec4;
-template <> struct Vec4<float> { typedef float4 T; };
-template <> struct Vec4<double> { typedef double4_32a T; };
+template <typename Real> using Vec4 = Real4T<Real>;
 
 // Tait pressure over rho^2 and sound speed, float64 form.
 __device__ __forceinline__ void eos64(const DevParams &P, double rho, double *pr, double *c)
@@ -413,8 +430,9 @@ __device__ __forceinline__ void cell_origin(const DevParams &P, const double *__
 // Threads [0, nf): particle q of the cell-grouped order (cell_q, src_q, id_q
 // from k_place) takes position p = start[c] + (number of particles of its cell
 // with a smaller id), which is its place in the (cell, id) order; its fluid
-// arrays are copied from buffer `src` to position p of buffer `dst` with the
-// packed PI inputs.  The ids of a cell are contiguous in id_q, so the rank
+// state (x, y, z, the records V and VM, id) is copied from buffer `src` to
+// position p of buffer `dst`, and its packed position record written.  The ids
+// of a cell are contiguous in id_q, so the rank
 // reads them from L1 (about 27 per cell at rest density; the cost grows with
 // the square of a cell's population).  Threads [nf, nf+nb): refresh the packed
 // pressure/density of boundary particle (i - nf).  Block max of the sound
@@ -424,14 +442,10 @@ __global__ void __launch_bounds__(256)
 k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
           const uint32_t *__restrict__ src_q, const uint32_t *__restrict__ id_q,
           const double *__restrict__ sx, const double *__restrict__ sy, const double *__restrict__ sz,
-          const Real *__restrict__ svx, const Real *__restrict__ svy, const Real *__restrict__ svz,
-          const Real *__restrict__ svmx, const Real *__restrict__ svmy, const Real *__restrict__ svmz,
-          const Real *__restrict__ srho, const Real *__restrict__ srhom, const uint32_t *__restrict__ sid,
+          const typename Vec4<Real>::T *__restrict__ sV, const typename Vec4<Real>::T *__restrict__ sVM,
           double *__restrict__ dx, double *__restrict__ dy, double *__restrict__ dz,
-          Real *__restrict__ dvx, Real *__restrict__ dvy, Real *__restrict__ dvz,
-          Real *__restrict__ dvmx, Real *__restrict__ dvmy, Real *__restrict__ dvmz,
-          Real *__restrict__ drho, Real *__restrict__ drhom, uint32_t *__restrict__ did,
-          typename Vec4<Real>::T *__restrict__ posp, typename Vec4<Real>::T *__restrict__ velr,
+          typename Vec4<Real>::T *__restrict__ dV, typename Vec4<Real>::T *__restrict__ dVM,
+          uint32_t *__restrict__ did, typename Vec4<Real>::T *__restrict__ posp,
           uint32_t *__restrict__ cell, const Real *__restrict__ brho,
           typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
           const int32_t *__restrict__ bstart, const int32_t *__restrict__ fstart,
@@ -452,9 +466,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
         const uint32_t myid = id_q[i];
         // the source loads are issued before the rank loop, which hides their latency
         const double x = sx[s], y = sy[s], z = sz[s];
-        const Real vx = svx[s], vy = svy[s], vz = svz[s];
-        const Real vmx = svmx[s], vmy = svmy[s], vmz = svmz[s];
-        const Real rho = srho[s], rhom = srhom[s];
+        const V4 vv = sV[s], vm = sVM[s];
         const int b = fstart[c], e = fstart[c + 1];
         int r = 0;
 #pragma unroll 4
@@ -463,12 +475,12 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
         // a PI work item starts at every 32nd particle of a cell
         if (c < P.ncells) item = (r & 31) == 0;
         dx[p] = x; dy[p] = y; dz[p] = z;
-        dvx[p] = vx; dvy[p] = vy; dvz[p] = vz;
-        dvmx[p] = vmx; dvmy[p] = vmy; dvmz[p] = vmz;
-        drho[p] = rho; drhom[p] = rhom;
+        dV[p] = vv;   // also the PI input velr = {v, rho}
+        dVM[p] = vm;
         did[p] = myid;
         cell[p] = c;
-        V4 pp, vv;
+        const Real rho = vv.w;
+        V4 pp;
         if (SPLIT) {
             float pr, cs;
             eos32(P, (float)rho, &pr, &cs);
@@ -487,9 +499,7 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
                 posf[p] = make_float4((float)(x - ox), (float)(y - oy), (float)(z - oz), 0.f);
             }
         }
-        vv.x = vx; vv.y = vy; vv.z = vz; vv.w = rho;
         posp[p] = pp;
-        velr[p] = vv;
     } else if (i < nf + nb) {
         int j = i - nf;
         if (j < bstart[P.ncells]) {
@@ -602,14 +612,19 @@ static int nl_fluid_t(sph_ctx *ctx)
     int nf = (int)ctx->nf, nb = (int)ctx->nb;
     int src = ctx->cur, dst = 1 - ctx->cur;
     const int T = 256;
-    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2 + kCtrReset), st)))
+    // one memset clears the cell counts, their tile sums and the work-item
+    // counters of this step (they follow each other in the workspace)
+    const int64_t ftiles = scan_tiles((int64_t)ctx->ncells + 2);
+    if (check_cuda(cudaMemsetAsync(w.count, 0,
+                                   sizeof(uint32_t) * (ctx->ncells + 2 + ftiles + kCtrReset), st)))
         return SPH_ERR_CUDA;
-    // cell and slot of every particle (key_tmp, val_tmp), counts per cell
+    // cell and slot of every particle (key_tmp, val_tmp), counts per cell and
+    // per scan tile
     if (nf > 0)
         SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src], nf,
-                   ctx->dp, w.key_tmp, w.val_tmp, w.count, w.sc);
-    int rc = exclusive_scan_u32(ctx, w.count, (uint32_t *)w.fstart, (int64_t)ctx->ncells + 2,
-                                w.scan_part, st);
+                   ctx->dp, w.key_tmp, w.val_tmp, w.count, w.fpart, w.sc);
+    int rc = exclusive_scan_down_u32(ctx, w.count, (uint32_t *)w.fstart,
+                                     (int64_t)ctx->ncells + 2, w.fpart, st);
     if (rc) return rc;
     // cell-grouped order: cell (key_sorted), source (val_sorted), id (key_by_id)
     if (nf > 0)
@@ -617,18 +632,13 @@ static int nl_fluid_t(sph_ctx *ctx)
                    w.fstart, w.key_sorted, w.val_sorted, w.key_by_id);
     int tot = nf + nb;
     if (tot > 0) {
+        typedef typename Vec4<Real>::T V4;
         SPH_LAUNCH(ctx, (k_reorder<Real, SPLIT>), (tot + T - 1) / T, T, 0, st, nf, nb, ctx->dp,
                    w.key_sorted, w.val_sorted, w.key_by_id, w.x[src], w.y[src], w.z[src],
-                   (const Real *)w.vx[src],
-                   (const Real *)w.vy[src], (const Real *)w.vz[src], (const Real *)w.vmx[src],
-                   (const Real *)w.vmy[src], (const Real *)w.vmz[src], (const Real *)w.rho[src],
-                   (const Real *)w.rhom[src], w.id[src], w.x[dst], w.y[dst], w.z[dst],
-                   (Real *)w.vx[dst], (Real *)w.vy[dst], (Real *)w.vz[dst], (Real *)w.vmx[dst],
-                   (Real *)w.vmy[dst], (Real *)w.vmz[dst], (Real *)w.rho[dst], (Real *)w.rhom[dst],
-                   w.id[dst], (typename Vec4<Real>::T *)w.posp, (typename Vec4<Real>::T *)w.velr,
-                   w.cell, (const Real *)w.brho, (typename Vec4<Real>::T *)w.bposp,
-                   (typename Vec4<Real>::T *)w.bvelr, w.bstart, w.fstart, w.items_f, w.ctr,
-                   w.origin, w.posf, w.sc);
+                   (const V4 *)w.V[src], (const V4 *)w.VM[src], w.x[dst], w.y[dst], w.z[dst],
+                   (V4 *)w.V[dst], (V4 *)w.VM[dst], w.id[dst], (V4 *)w.posp, w.cell,
+                   (const Real *)w.brho, (V4 *)w.bposp, (V4 *)w.bvelr, w.bstart, w.fstart,
+                   w.items_f, w.ctr, w.origin, w.posf, w.sc);
     }
     ctx->cur = dst;
     return check_cuda(cudaGetLastError());
@@ -653,7 +663,11 @@ static int nl_boundary_t(sph_ctx *ctx)
     const double *in_rho = w.stage + 6 * N;
     const double *in_rhom = w.stage + 10 * N;
     const int T = 256;
-    if (check_cuda(cudaMemsetAsync(w.count, 0, sizeof(uint32_t) * (ctx->ncells + 2 + kCtrWords), st)))
+    if (check_cuda(cudaMemsetAsync(w.count, 0,
+                                   sizeof(uint32_t) * (ctx->ncells + 2 +
+                                                       scan_tiles((int64_t)ctx->ncells + 2) +
+                                                       kCtrWords),
+                                   st)))
         return SPH_ERR_CUDA;
     if (nb > 0) {
         SPH_LAUNCH(ctx, k_boundary_hash, (nb + T - 1) / T, T, 0, st, in_pos, (uint32_t)nf, nb,

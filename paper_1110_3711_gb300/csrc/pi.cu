@@ -309,7 +309,7 @@ __device__ __forceinline__ void pi64_item(
 {
     const witems::Item I = witems::item_of<MOMENTUM>(P, items, it, tcell, tstart, lane);
     const int i = I.i;
-    const witems::Frame Fr = witems::frame_of<MOMENTUM>(P, I, tposf[i], tcell);
+    const witems::Frame Fr = witems::frame_of<MOMENTUM>(P, I, tposf[i], tcell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // the target this lane works for in the balanced walk, its sums, and the
     // lane's own target's total
@@ -427,19 +427,19 @@ int pi_launch(sph_ctx *ctx)
         if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, sizeof(uint32_t), st))) return SPH_ERR_CUDA;
         SPH_LAUNCH(ctx, k_pi64w, ctx->pi_grid_f, W64_WARPS * 32, 0, st, ctx->dp, nf, nb,
                    w.items_f, w.items_b, w.ctr, nb > 0 ? 1 : 0, &w.ctr[1],
-                   (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.posf, w.cell,
+                   (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx), w.posf, w.cell,
                    w.fstart, (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bposf,
                    w.bcell, w.bstart, (double4_32a *)w.acc, (double *)w.bar, w.sc);
     } else {
         if (nf > 0)
             SPH_LAUNCH(ctx, k_pi_fluid64, (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
-                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.cell, w.fstart,
+                       (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx), w.cell, w.fstart,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bstart,
                        w.posf, w.bposf, (double4_32a *)w.acc, w.sc);
         if (nb > 0)
             SPH_LAUNCH(ctx, k_pi_boundary64, (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const double4_32a *)w.bposp, (const double4_32a *)w.bvelr, w.bcell, w.bstart,
-                       (const double4_32a *)w.posp, (const double4_32a *)w.velr, w.fstart, w.bposf,
+                       (const double4_32a *)w.posp, (const double4_32a *)velr_of(ctx), w.fstart, w.bposf,
                        w.posf, (double *)w.bar, w.sc);
     }
     return check_cuda(cudaGetLastError());

@@ -22,7 +22,7 @@
 //   boundary:  all 9 rows, evaluated for both particles (the B-F continuity
 //              term of a boundary particle is the b side of an F-B pair), so no
 //              separate boundary-target kernel runs.
-// Staging, the lockstep distance test and the per-lane hit walk are those of
+// The lockstep distance test (warp_items.cuh) and the per-lane hit walk are those of
 // the warp kernel, in units of h with the constants folded out of the loop.
 // The b-side terms of a pass are summed per staged candidate in shared memory
 // (lanes that reach the same candidate in the same iteration take turns, the
@@ -43,6 +43,7 @@
 
 #include "pair32.cuh"
 #include "sph_internal.cuh"
+#include "warp_items.cuh"
 
 namespace sph {
 
@@ -121,7 +122,6 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
         const int cy = (int)(cyz % (uint32_t)P.ny);
         const int cz = (int)(cyz / (uint32_t)P.ny);
         const float xa = pa.x * P.invhf, ya = pa.y * P.invhf, za = pa.z * P.invhf;
-        const float m2x = -2.0f * xa, m2y = -2.0f * ya, m2z = -2.0f * za;
         const float thr = active ? 4.0f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
         const float ra = va.w * P.inv_rho0f;
         const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
@@ -230,19 +230,7 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
             }
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
-            for (int q = 0; q < nch; ++q) {
-                uint32_t lo = 0u, hi = 0u;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float4 a = S.A[q * 32 + k];
-                    const float4 b = S.A[q * 32 + 16 + k];
-                    const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - thr;
-                    const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - thr;
-                    lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-                    hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
-                }
-                S.M[q][lane] = __brev((lo << 16) | hi);
-            }
+            witems::lockstep_tests(S.A, S.M, nch, lane, witems::Frame{xa, ya, za, thr});
             // ---- every lane walks its own hits; b-side terms to the candidate's
             // slot.  All lanes iterate together (until no lane has a hit left)
             // so that the warp-wide match below is well defined.
@@ -380,7 +368,7 @@ int pi32_sym_launch(sph_ctx *ctx)
     if (nf > 0) {
         if (check_cuda(cudaMemsetAsync(&w.ctr[1], 0, sizeof(uint32_t), st))) return SPH_ERR_CUDA;
         SPH_LAUNCH(ctx, k_pi32_sym, ctx->pi_grid_f, WARPS * 32, 0, st, ctx->dp, w.items_f,
-                   &w.ctr[0], &w.ctr[1], (const float4 *)w.posp, (const float4 *)w.velr, w.cell,
+                   &w.ctr[0], &w.ctr[1], (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.cell,
                    w.fstart, (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart,
                    (float4 *)w.acc, (float *)w.bar, w.sc);
     }

@@ -198,17 +198,17 @@ int pi32_thread_launch(sph_ctx *ctx)
     if (nf > 0) {
         if (fast)
             SPH_LAUNCH(ctx, (k_pi_thread_fluid<true, 1>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart, w.franges,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.cell, w.fstart, w.franges,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bstart, w.branges,
                        (float4 *)w.acc, w.sc);
         else if (ctx->dp.reach == 1)
             SPH_LAUNCH(ctx, (k_pi_thread_fluid<false, 1>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.cell, w.fstart,
                        (const int4 *)nullptr, (const float4 *)w.bposp, (const float4 *)w.bvelr,
                        w.bstart, (const int4 *)nullptr, (float4 *)w.acc, w.sc);
         else
             SPH_LAUNCH(ctx, (k_pi_thread_fluid<false, 2>), (nf + T - 1) / T, T, 0, st, nf, ctx->dp,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.cell, w.fstart,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.cell, w.fstart,
                        (const int4 *)nullptr, (const float4 *)w.bposp, (const float4 *)w.bvelr,
                        w.bstart, (const int4 *)nullptr, (float4 *)w.acc, w.sc);
     }
@@ -216,17 +216,17 @@ int pi32_thread_launch(sph_ctx *ctx)
         if (fast)
             SPH_LAUNCH(ctx, (k_pi_thread_boundary<true, 1>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart, w.franges,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.fstart, w.franges,
                        (float *)w.bar, w.sc);
         else if (ctx->dp.reach == 1)
             SPH_LAUNCH(ctx, (k_pi_thread_boundary<false, 1>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.fstart,
                        (const int4 *)nullptr, (float *)w.bar, w.sc);
         else
             SPH_LAUNCH(ctx, (k_pi_thread_boundary<false, 2>), (nb + T - 1) / T, T, 0, st, nb, ctx->dp,
                        (const float4 *)w.bposp, (const float4 *)w.bvelr, w.bcell, w.bstart,
-                       (const float4 *)w.posp, (const float4 *)w.velr, w.fstart,
+                       (const float4 *)w.posp, (const float4 *)velr_of(ctx), w.fstart,
                        (const int4 *)nullptr, (float *)w.bar, w.sc);
     }
     return check_cuda(cudaGetLastError());

@@ -1,12 +1,14 @@
 // Internal declarations of libsph (not part of the ABI).
 //
 // Data layout in HBM (one context):
-//   fluid state, double-buffered (NL gathers buffer `cur` into `1-cur`), SoA in
-//   sorted (cell, id) order:  x y z (f64) | vx vy vz | vmx vmy vmz | rho rhom
-//   (Real = f64 in SPH_FP64, f32 in SPH_FP32_SPLIT) | id (u32)
-//   packed PI inputs of Section 4.3: posp = {x, y, z, P/rho^2}, velr = {vx, vy,
-//   vz, rho}; in SPH_FP32_SPLIT the position is the f32 offset from the origin
-//   of the particle's cell, in SPH_FP64 it is absolute.  cell (u32) per particle.
+//   fluid state, double-buffered (NL gathers buffer `cur` into `1-cur`), in
+//   sorted (cell, id) order:  x y z (f64, one array each) | V = {vx, vy, vz,
+//   rho} | VM = {vx, vy, vz, rho} of the previous level (Real4 records, Real =
+//   f64 in SPH_FP64, f32 in SPH_FP32_SPLIT) | id (u32).
+//   packed PI inputs of Section 4.3: posp = {x, y, z, P/rho^2} (written by NL)
+//   and velr = {vx, vy, vz, rho}, which is V of the current buffer itself; in
+//   SPH_FP32_SPLIT the position is the f32 offset from the origin of the
+//   particle's cell, in SPH_FP64 it is absolute.  cell (u32) per particle.
 //   PI output acc = {ax, ay, az, drho/dt} per fluid particle.
 //   boundary state (never moves, sorted once): x y z (f64), rho rhom (Real),
 //   id (u32), packed posp/velr like the fluid, ar (Real) output.
@@ -72,12 +74,12 @@ struct DevParams {
 struct Workspace {
     // fluid state
     double *x[2], *y[2], *z[2];
-    void *vx[2], *vy[2], *vz[2], *vmx[2], *vmy[2], *vmz[2], *rho[2], *rhom[2];
+    void *V[2], *VM[2];       // Real4 {vx, vy, vz, rho} of this and of the previous level
     uint32_t *id[2];
     char *state_chunk[2];
     size_t state_chunk_bytes;
-    // packed PI inputs / outputs (fluid)
-    void *posp, *velr, *acc;
+    // packed PI inputs / outputs (fluid); the velocity record is V[cur]
+    void *posp, *acc;
     float4 *posf, *bposf;     // SPH_FP64: float32 offsets from the cell origin (pre-test of PI)
     uint32_t *cell;
     // boundary
@@ -90,7 +92,8 @@ struct Workspace {
     // key_sorted / val_sorted / key_by_id = cell / source / id in the
     // cell-grouped order.  Boundary: the radix sort's keys and values.
     uint32_t *key_by_id, *val_by_id, *key_tmp, *val_tmp, *key_sorted, *val_sorted;
-    uint32_t *count;          // [ncells + 2], then the work-item counters ctr
+    uint32_t *count;          // [ncells + 2], then fpart, then the work-item counters ctr
+    uint32_t *fpart;          // fluid NL: particles per scan tile of kScanTile cells (k_hash)
     uint32_t *ctr;            // [0] fluid items, [1] next item of the PI queue, [2] spare, [3] boundary items
     uint32_t *items_f, *items_b;  // PI work items: fluid, first target of a (cell, 32-target chunk);
                                   // boundary, {first, count} of packed cells of one x row
@@ -139,6 +142,14 @@ struct sph_ctx {
 };
 
 namespace sph {
+
+// {v, rho} records of the current fluid state: the PI input velr of Section 4.3.
+inline void *velr_of(const sph_ctx *ctx) { return ctx->w.V[ctx->cur]; }
+
+// Four-component record of the precision of a form.
+template <typename Real> struct Real4T;
+template <> struct Real4T<float> { typedef float4 T; };
+template <> struct Real4T<double> { typedef double4_32a T; };
 
 // workspace planning (api.cu)
 size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], uint32_t *ncells,
@@ -191,6 +202,12 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *partials, cudaStream_t st);
+// The down-sweep of exclusive_scan_u32 alone, for tile sums (partials) the
+// caller has already formed.
+int exclusive_scan_down_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
+                            const uint32_t *partials, cudaStream_t st);
+// Tiles of kScanTile entries in a scan of n entries.
+inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *dst, double v)
 {

@@ -45,20 +45,16 @@ __device__ __forceinline__ double widen(float f)
 }
 __device__ __forceinline__ double widen(double f) { return f; }
 
-template <typename Real> struct V4T;
-template <> struct V4T<float> { typedef float4 T; };
-template <> struct V4T<double> { typedef double4_32a T; };
-
 // Fluid particles in blocks [0, fblocks), boundary particles after them.
 template <typename Real>
 __global__ void __launch_bounds__(256)
 k_su(int nf, int nb, int fblocks, DevParams P, const int32_t *__restrict__ fstart,
      const int32_t *__restrict__ bstart, double *__restrict__ x, double *__restrict__ y,
-     double *__restrict__ z, Real *__restrict__ vx, Real *__restrict__ vy, Real *__restrict__ vz,
-     Real *__restrict__ vmx, Real *__restrict__ vmy, Real *__restrict__ vmz,
-     Real *__restrict__ rho, Real *__restrict__ rhom, const typename V4T<Real>::T *__restrict__ acc,
+     double *__restrict__ z, typename Real4T<Real>::T *__restrict__ V,
+     typename Real4T<Real>::T *__restrict__ VM, const typename Real4T<Real>::T *__restrict__ acc,
      Real *__restrict__ brho, Real *__restrict__ brhom, const Real *__restrict__ bar, Scalars *sc)
 {
+    typedef typename Real4T<Real>::T R4;
     // dt and its multiples in the precision of the form, once per block
     __shared__ Real sdt[3];
     __shared__ int seuler;
@@ -75,31 +71,29 @@ k_su(int nf, int nb, int fblocks, DevParams P, const int32_t *__restrict__ fstar
     if ((int)blockIdx.x < fblocks) {
         const int i = blockIdx.x * blockDim.x + threadIdx.x;
         if (i < nf && i < fstart[P.ncells]) {
-            typename V4T<Real>::T f = acc[i];
-            Real v0 = vx[i], v1 = vy[i], v2 = vz[i];
+            const R4 f = acc[i];
+            const R4 v = V[i];
             // x^{n+1} = x^n + (dt v^n + dt^2/2 F^n): the increment in the precision
             // of the form, the accumulation always in float64
-            x[i] = x[i] + widen(dtr * v0 + hdt2 * f.x);
-            y[i] = y[i] + widen(dtr * v1 + hdt2 * f.y);
-            z[i] = z[i] + widen(dtr * v2 + hdt2 * f.z);
-            Real r = rho[i];
-            Real nv0, nv1, nv2, nr;
+            x[i] = x[i] + widen(dtr * v.x + hdt2 * f.x);
+            y[i] = y[i] + widen(dtr * v.y + hdt2 * f.y);
+            z[i] = z[i] + widen(dtr * v.z + hdt2 * f.z);
+            R4 nv;
             if (seuler) {
-                nv0 = v0 + dtr * f.x;
-                nv1 = v1 + dtr * f.y;
-                nv2 = v2 + dtr * f.z;
-                nr = r + dtr * f.w;
+                nv.x = v.x + dtr * f.x;
+                nv.y = v.y + dtr * f.y;
+                nv.z = v.z + dtr * f.z;
+                nv.w = v.w + dtr * f.w;
             } else {
-                nv0 = vmx[i] + dt2 * f.x;
-                nv1 = vmy[i] + dt2 * f.y;
-                nv2 = vmz[i] + dt2 * f.z;
-                nr = rhom[i] + dt2 * f.w;
+                const R4 u = VM[i];
+                nv.x = u.x + dt2 * f.x;
+                nv.y = u.y + dt2 * f.y;
+                nv.z = u.z + dt2 * f.z;
+                nv.w = u.w + dt2 * f.w;
             }
-            vmx[i] = v0; vmy[i] = v1; vmz[i] = v2;
-            vx[i] = nv0; vy[i] = nv1; vz[i] = nv2;
-            rhom[i] = r;
-            rho[i] = nr;
-            nan = !(nr == nr) || !(nv0 == nv0) || !(nv1 == nv1) || !(nv2 == nv2);
+            VM[i] = v;
+            V[i] = nv;
+            nan = !(nv.w == nv.w) || !(nv.x == nv.x) || !(nv.y == nv.y) || !(nv.z == nv.z);
         }
     } else {
         const int i = (blockIdx.x - fblocks) * blockDim.x + threadIdx.x;
@@ -138,10 +132,9 @@ static int su_t(sph_ctx *ctx)
     const int T = 256;
     const int fblocks = (nf + T - 1) / T, bblocks = (nb + T - 1) / T;
     SPH_LAUNCH(ctx, k_su<Real>, fblocks + bblocks > 0 ? fblocks + bblocks : 1, T, 0, st, nf, nb,
-               fblocks, ctx->dp, w.fstart, w.bstart, w.x[c], w.y[c], w.z[c], (Real *)w.vx[c],
-               (Real *)w.vy[c], (Real *)w.vz[c], (Real *)w.vmx[c], (Real *)w.vmy[c],
-               (Real *)w.vmz[c], (Real *)w.rho[c], (Real *)w.rhom[c],
-               (const typename V4T<Real>::T *)w.acc, (Real *)w.brho, (Real *)w.brhom,
+               fblocks, ctx->dp, w.fstart, w.bstart, w.x[c], w.y[c], w.z[c],
+               (typename Real4T<Real>::T *)w.V[c], (typename Real4T<Real>::T *)w.VM[c],
+               (const typename Real4T<Real>::T *)w.acc, (Real *)w.brho, (Real *)w.brhom,
                (const Real *)w.bar, w.sc);
     SPH_LAUNCH(ctx, k_finalize, 1, 1, 0, st, ctx->dp, w.sc);
     return check_cuda(cudaGetLastError());

@@ -1,5 +1,6 @@
-// Warp-per-work-item candidate search shared by the float64 kernels (PI and
-// its adjoint).
+// Warp-per-work-item candidate search of the PI kernels: the float32 warp
+// kernel (pi32.cu), the float64 PI (pi.cu) and its adjoint (adjoint.cu); the
+// symmetric float32 variant (pi32_sym.cu) shares the lockstep test.
 //
 // A work item is up to 32 fluid targets of one cell (items_f, one entry per
 // first target) or up to 32 boundary targets of consecutive cells of one x
@@ -7,20 +8,24 @@
 //   1. builds the table of its x-runs (Section 4.4, Fig. 10): for every
 //      (dy, dz) of the 9 neighbour rows, cells x-1 .. x+1 (of the item's first
 //      and last cell) are one index range of the fluid list, and for fluid
-//      targets of the boundary list too;
+//      targets of the boundary list too (build_runs);
 //   2. stages the candidates of those runs that lie within 2h of the targets'
-//      bounding box in shared memory, as their float32 cell-relative offsets
-//      shifted into the frame of the item's first cell, in units of h, with
-//      |x|^2 beside them, and their indices;
-//   3. tests every candidate against every target in lockstep, in float32,
-//      against 4 (1 + 1e-4) (units of h^2): the float32 error of the offsets
-//      and of the test is below 1e-5 of 4, so every pair of the float64 test
-//      r^2 < 4h^2 is a hit (the float64 test then decides);
-//   4. lets every lane walk its own hits in staging order, calling the
-//      caller's hit function with the candidate's index and list.
+//      bounding box (target_box) in shared memory, as their float32
+//      cell-relative offsets shifted into the frame of the item's first cell,
+//      in units of h, with |x|^2 beside them, and whatever else the kernel
+//      needs of them (stage_set);
+//   3. tests every candidate against every target in lockstep (lockstep_tests):
+//      the warp reads one candidate (a shared-memory broadcast) and each lane
+//      evaluates |x_b|^2 - 2 x_a.x_b - (thr0 - |x_a|^2), negative when
+//      |x_a - x_b|^2 < thr0 h^2 up to float32 rounding, and shifts its sign
+//      into a hit mask.  The float32 kernel takes thr0 = 4 (the test decides
+//      its pairs); the float64 kernels take 4 (1 + 1e-4): the float32 error of
+//      the offsets and of the test is below 1e-5 of 4, so every pair of their
+//      float64 test r^2 < 4h^2 is a hit (the float64 test then decides);
+//   4. lets every lane walk its own hits in staging order.
 // Neighbourhoods of more candidates than a pass holds take several passes;
-// pass p samples candidates p, p + npass, ..., so that each pass holds about
-// 1/npass of every lane's neighbours.  The walk order depends only on the item, so
+// pass p samples blocks p, p + npass, ... of BLK consecutive candidates, so
+// that each pass holds about 1/npass of every lane's neighbours.  The walk order depends only on the item, so
 // sums accumulated in it are deterministic.  Cells of edge 2h or more only.
 #pragma once
 
@@ -35,13 +40,47 @@ constexpr int NRUN = 18;   // 9 fluid + 9 boundary x-runs
 
 constexpr int RAW_PER_PASS = 2 * CAP;  // candidates sampled per pass (before the box test)
 
+// Passes sample the item's candidates in blocks of BLK consecutive ones: pass
+// p takes blocks p, p + npass, p + 2 npass, ...  A block of 8 records of 16
+// bytes is one 128-byte line, so each pass loads whole lines and no sector is
+// fetched by two passes, while every pass still samples the whole
+// neighbourhood (the hit walks stay balanced).
+#ifndef SPH_PASS_BLOCK
+#define SPH_PASS_BLOCK 8
+#endif
+constexpr int BLK = SPH_PASS_BLOCK;
+
+// Sample slots of pass `pass` of npass over K candidates (a multiple of BLK;
+// slots past the last candidate are empty).
+__device__ __forceinline__ int pass_slots(int K, int npass, int pass)
+{
+    const int nblk = (K + BLK - 1) / BLK;
+    return nblk > pass ? BLK * ((nblk - pass + npass - 1) / npass) : 0;
+}
+
+// Candidate index (0 .. K-1 over the item's runs) of sample slot ls of a pass.
+__device__ __forceinline__ int pass_candidate(int ls, int npass, int pass)
+{
+    return (pass + npass * (ls / BLK)) * BLK + ls % BLK;
+}
+
+// Box-test threshold (units of h^2): above the float32 error of the box
+// distance and of the lockstep test, so that no hit of either form is lost.
+constexpr float BOX_THR = 4.0004f;
+
+// The item's x-runs and its targets' bounding box.
+struct RunTable {
+    int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
+    int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
+    float box[6];           // targets' bounding box: min x, max x, min y, max y, min z, max z
+};
+
+// Staged candidates of the float64 kernels.
 struct Smem {
     float4 A[CAP];          // shifted offset {x, y, z} (units of h) and |x|^2
     uint32_t J[CAP];        // candidate index, bit 31 set for the boundary list
     uint32_t M[NCH][32];    // hit bits of lane l for chunk q
-    int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
-    int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
-    float box[6];           // targets' bounding box: min x, max x, min y, max y, min z, max z
+    RunTable T;
     int hincl[32];          // balanced walk: hits of targets 0 .. t of the tested set
 };
 
@@ -81,27 +120,174 @@ __device__ __forceinline__ Item item_of(const DevParams &P, const uint32_t *__re
 }
 
 // Lane's target in the item's frame (units of h): x, y, z and the test
-// threshold 4 (1 + 1e-4) - |x|^2 (-inf for idle lanes).
+// threshold thr0 - |x|^2 (-inf for idle lanes).
 struct Frame {
     float x, y, z, thr;
 };
 
 template <bool FLUID_TARGETS>
 __device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, const float4 &fa,
-                                          const uint32_t *__restrict__ tcell)
+                                          const uint32_t *__restrict__ tcell, float thr0)
 {
     Frame F;
     const float tshift = FLUID_TARGETS ? 0.0f : (float)(int)(tcell[I.i] - I.c) * P.s_hf;
     F.x = fmaf(fa.x, P.invhf, tshift);
     F.y = fa.y * P.invhf;
     F.z = fa.z * P.invhf;
-    F.thr = I.active ? 4.0004f - fmaf(F.x, F.x, fmaf(F.y, F.y, F.z * F.z)) : -INFINITY;
+    F.thr = I.active ? thr0 - fmaf(F.x, F.x, fmaf(F.y, F.y, F.z * F.z)) : -INFINITY;
     return F;
 }
 
-// Steps 1-3 above; after each staged set is tested, flush(nch) runs with the
-// hit masks of its nch chunks in S.M (lane l's bit k of S.M[q][l]: candidate
-// q * 32 + k is a hit of target l).  Every lane of the warp must call it.
+// Step 1: lane r describes run r of the table; returns the number of
+// candidates K.  b1, b2 of a run: for fluid targets the first indices of
+// cells x and x + 1 of its row (a candidate's x shift follows from its index);
+// for boundary targets the cell id of the item's first cell in that row.
+template <bool FLUID_TARGETS>
+__device__ __forceinline__ int build_runs(const DevParams &P, RunTable &T, int lane, const Item &I,
+                                          const int32_t *__restrict__ fstart,
+                                          const int32_t *__restrict__ bstart)
+{
+    const int nlists = FLUID_TARGETS ? 2 : 1;
+    const int r = lane;
+    int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
+    if (r < 9 * nlists) {
+        const int list = r / 9, q = r % 9;
+        const int dz = q / 3 - 1, dy = q % 3 - 1;
+        const int y = I.cy + dy, z = I.cz + dz;
+        code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
+        if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
+            const int32_t *st = list ? bstart : fstart;
+            const int row = P.nx * (y + P.ny * z);
+            const int x0 = max(I.cx - 1, 0), x1 = min(I.cx1 + 1, P.nx - 1);
+            j0 = st[row + x0];
+            L = st[row + x1 + 1] - j0;
+            if (FLUID_TARGETS) {
+                b1 = st[row + I.cx];       // first index of cell x
+                b2 = st[row + I.cx + 1];   // first index of cell x + 1
+            } else {
+                b1 = row + I.cx;           // cell id of the item's first cell in this row
+            }
+        }
+    }
+    int pe = L;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, pe, o);
+        if (lane >= o) pe += t;
+    }
+    if (r < NRUN) {
+        T.run[r] = make_int4(pe, j0, b1, b2);
+        T.code[r] = code;
+    }
+    const int K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
+    __syncwarp();
+    return K;
+}
+
+// The bounding box of the item's active targets (units of h, item frame).
+__device__ __forceinline__ void target_box(RunTable &T, int lane, const Frame &F)
+{
+    const bool act = F.thr > -INFINITY;
+    float b[6] = {act ? F.x : INFINITY, act ? F.x : -INFINITY, act ? F.y : INFINITY,
+                  act ? F.y : -INFINITY, act ? F.z : INFINITY, act ? F.z : -INFINITY};
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            b[2 * d] = fminf(b[2 * d], __shfl_xor_sync(0xffffffffu, b[2 * d], o));
+            b[2 * d + 1] = fmaxf(b[2 * d + 1], __shfl_xor_sync(0xffffffffu, b[2 * d + 1], o));
+        }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int d = 0; d < 6; ++d) T.box[d] = b[d];
+    }
+    __syncwarp();
+}
+
+// Step 3 for the nch chunks of 32 staged candidates in A (their w is |x|^2):
+// bit k of M[q][lane] is set when candidate q * 32 + k is a hit of this
+// lane's target.  The sign of t - thr is shifted into two independent
+// 16-candidate masks (candidate k lands at bit 15 - k of its half), which are
+// joined and bit-reversed so that candidate k ends at bit k.
+__device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32], int nch,
+                                               int lane, const Frame &F)
+{
+    const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
+    for (int q = 0; q < nch; ++q) {
+        uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const float4 a = A[q * 32 + k];
+            const float4 b = A[q * 32 + 16 + k];
+            const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
+            const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
+            lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+            hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+        }
+        M[q][lane] = __brev((lo << 16) | hi);
+    }
+}
+
+// Step 2 for one set: sample slots k0, k0 + 1, ... of pass `pass` (np slots,
+// K candidates in the item) are taken 32 at a time while the set may take
+// another 32 (at most cap); the candidates within 2h of the box are packed by
+// a ballot into slots 0 .. n-1 and n is returned.  k0 and r (the current run,
+// which only moves forward) carry over to the next set.
+//   load(j, blist) issues the loads of candidate j of its list and returns
+//                  them; its member pos is the float32 offset record (metres)
+//   store(slot, a, c) writes the kept candidate: a = shifted offset {x, y, z}
+//                  in units of h and |x|^2, c what load returned
+template <bool FLUID_TARGETS, class Load, class Store>
+__device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, int lane, int cap,
+                                         int pass, int npass, int np, int K, int &k0, int &r,
+                                         const uint32_t *__restrict__ fcell, Load &&load,
+                                         Store &&store)
+{
+    typedef decltype(load(0, false)) Cand;
+    // the box is uniform over the warp: held in registers for the whole set
+    const float bx0 = T.box[0], bx1 = T.box[1], by0 = T.box[2], by1 = T.box[3],
+                bz0 = T.box[4], bz1 = T.box[5];
+    int n = 0;
+    while (k0 < np && n <= cap - 32) {
+        const int ls = k0 + lane;
+        const int sidx = pass_candidate(ls, npass, pass);
+        bool keep = false;
+        float4 a;
+        Cand c;
+        if (ls < np && sidx < K) {
+            while (sidx >= T.run[r].x) ++r;
+            const int4 ri = T.run[r];
+            const int prev = r ? T.run[r - 1].x : 0;
+            const int j = ri.y + (sidx - prev);
+            const int cd = T.code[r];
+            const float sx = FLUID_TARGETS ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
+                                           : (float)((int)fcell[j] - ri.z) * P.s_hf;
+            const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
+            const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
+            c = load(j, FLUID_TARGETS && (cd & 1));
+            a.x = fmaf(c.pos.x, P.invhf, sx);
+            a.y = fmaf(c.pos.y, P.invhf, sy);
+            a.z = fmaf(c.pos.z, P.invhf, sz);
+            const float dx = fmaxf(fmaxf(bx0 - a.x, a.x - bx1), 0.0f);
+            const float dy = fmaxf(fmaxf(by0 - a.y, a.y - by1), 0.0f);
+            const float dz = fmaxf(fmaxf(bz0 - a.z, a.z - bz1), 0.0f);
+            keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < BOX_THR;
+            if (keep) a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
+        }
+        const unsigned ball = __ballot_sync(0xffffffffu, keep);
+        if (keep) store(n + __popc(ball & ((1u << lane) - 1u)), a, c);
+        n += __popc(ball);
+        k0 += 32;
+    }
+    return n;
+}
+
+// Steps 1-3 above for the float64 kernels (candidates from the float32
+// offsets fposf / bposf); after each staged set is tested, flush(nch) runs
+// with the hit masks of its nch chunks in S.M (lane l's bit k of S.M[q][l]:
+// candidate q * 32 + k is a hit of target l) and the candidates' indices in
+// S.J.  Every lane of the warp must call it.
 template <bool FLUID_TARGETS, class Flush>
 __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int lane,
                                                const Item &I, const Frame &F,
@@ -111,114 +297,29 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
                                                const float4 *__restrict__ bposf,
                                                const uint32_t *__restrict__ fcell, Flush &&flush)
 {
-    const int nlists = FLUID_TARGETS ? 2 : 1;
-    int K;
-    {
-        const int r = lane;
-        int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
-        if (r < 9 * nlists) {
-            const int list = r / 9, q = r % 9;
-            const int dz = q / 3 - 1, dy = q % 3 - 1;
-            const int y = I.cy + dy, z = I.cz + dz;
-            code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
-            if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
-                const int32_t *st = list ? bstart : fstart;
-                const int row = P.nx * (y + P.ny * z);
-                const int x0 = max(I.cx - 1, 0), x1 = min(I.cx1 + 1, P.nx - 1);
-                j0 = st[row + x0];
-                L = st[row + x1 + 1] - j0;
-                if (FLUID_TARGETS) {
-                    b1 = st[row + I.cx];       // first index of cell x
-                    b2 = st[row + I.cx + 1];   // first index of cell x + 1
-                } else {
-                    b1 = row + I.cx;           // cell id of the item's first cell in this row
-                }
-            }
-        }
-        int pe = L;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, pe, o);
-            if (lane >= o) pe += t;
-        }
-        if (r < NRUN) {
-            S.run[r] = make_int4(pe, j0, b1, b2);
-            S.code[r] = code;
-        }
-        K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
-    }
-    __syncwarp();
-
-    // bounding box of the item's targets (units of h, item frame)
-    {
-        const bool act = F.thr > -INFINITY;
-        float b[6] = {act ? F.x : INFINITY, act ? F.x : -INFINITY, act ? F.y : INFINITY,
-                      act ? F.y : -INFINITY, act ? F.z : INFINITY, act ? F.z : -INFINITY};
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                b[2 * d] = fminf(b[2 * d], __shfl_xor_sync(0xffffffffu, b[2 * d], o));
-                b[2 * d + 1] = fmaxf(b[2 * d + 1], __shfl_xor_sync(0xffffffffu, b[2 * d + 1], o));
-            }
-        }
-        if (lane == 0) {
-#pragma unroll
-            for (int d = 0; d < 6; ++d) S.box[d] = b[d];
-        }
-        __syncwarp();
-    }
-
-    const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
-    // Pass p takes candidates p, p + npass, ... (an interleaved sample of the
-    // whole neighbourhood); only those within 2h of the targets' bounding box
-    // are staged (the box test's threshold 4.0004 h^2 lies above its float32
-    // error), packed with a ballot, and the staged set is tested and walked
-    // whenever it may not take another 32.
+    const int K = build_runs<FLUID_TARGETS>(P, S.T, lane, I, fstart, bstart);
+    target_box(S.T, lane, F);
+    struct Cand {
+        float4 pos;
+        uint32_t jj;
+    };
+    auto load = [&](int j, bool blist) {
+        Cand c;
+        c.pos = blist ? bposf[j] : fposf[j];
+        c.jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
+        return c;
+    };
+    auto store = [&](int slot, const float4 &a, const Cand &c) {
+        S.A[slot] = a;
+        S.J[slot] = c.jj;
+    };
     const int npass = (K + RAW_PER_PASS - 1) / RAW_PER_PASS;
     for (int pass = 0; pass < npass; ++pass) {
-        const int np = (K - pass + npass - 1) / npass;
+        const int np = pass_slots(K, npass, pass);
         int k0 = 0, r = 0;
         while (k0 < np) {
-            int n = 0;
-            while (k0 < np && n <= CAP - 32) {
-                const int ls = k0 + lane;
-                bool keep = false;
-                float4 a;
-                uint32_t jj = 0;
-                if (ls < np) {
-                    const int sidx = pass + npass * ls;
-                    while (sidx >= S.run[r].x) ++r;
-                    const int4 ri = S.run[r];
-                    const int prev = r ? S.run[r - 1].x : 0;
-                    const int j = ri.y + (sidx - prev);
-                    const int cd = S.code[r];
-                    const float sx = FLUID_TARGETS
-                                         ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
-                                         : (float)((int)fcell[j] - ri.z) * P.s_hf;
-                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-                    const bool blist = FLUID_TARGETS && (cd & 1);
-                    const float4 f = blist ? bposf[j] : fposf[j];
-                    a.x = fmaf(f.x, P.invhf, sx);
-                    a.y = fmaf(f.y, P.invhf, sy);
-                    a.z = fmaf(f.z, P.invhf, sz);
-                    const float dx = fmaxf(fmaxf(S.box[0] - a.x, a.x - S.box[1]), 0.0f);
-                    const float dy = fmaxf(fmaxf(S.box[2] - a.y, a.y - S.box[3]), 0.0f);
-                    const float dz = fmaxf(fmaxf(S.box[4] - a.z, a.z - S.box[5]), 0.0f);
-                    keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < 4.0004f;
-                    a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                    jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
-                }
-                const unsigned ball = __ballot_sync(0xffffffffu, keep);
-                if (keep) {
-                    const int slot = n + __popc(ball & ((1u << lane) - 1u));
-                    S.A[slot] = a;
-                    S.J[slot] = jj;
-                }
-                n += __popc(ball);
-                k0 += 32;
-            }
+            const int n = stage_set<FLUID_TARGETS>(P, S.T, lane, CAP, pass, npass, np, K, k0, r,
+                                                   fcell, load, store);
             // far candidates fill the last chunk
             const int nch = (n + 31) >> 5;
             if (n + lane < nch * 32) {
@@ -226,21 +327,7 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
                 S.J[n + lane] = 0u;
             }
             __syncwarp();
-            // lockstep tests: the sign of t - thr is the hit bit, shifted into two
-            // 16-candidate masks that are joined and bit-reversed (candidate k at bit k)
-            for (int q = 0; q < nch; ++q) {
-                uint32_t lo = 0u, hi = 0u;
-#pragma unroll
-                for (int k = 0; k < 16; ++k) {
-                    const float4 a = S.A[q * 32 + k];
-                    const float4 b = S.A[q * 32 + 16 + k];
-                    const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
-                    const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
-                    lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-                    hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
-                }
-                S.M[q][lane] = __brev((lo << 16) | hi);
-            }
+            lockstep_tests(S.A, S.M, nch, lane, F);
             __syncwarp();
             flush(nch);
             __syncwarp();
