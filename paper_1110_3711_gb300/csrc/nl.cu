@@ -28,6 +28,9 @@
 
 namespace sph {
 
+constexpr int kHashBlock = 512;   // threads (particles) per k_hash block
+constexpr int kHashTiles = 4;     // scan tiles a block counts in shared memory
+
 // ------------------------------------------------------------------ cells --
 
 // float32 value of x with its 24 leading significand bits (the rest cut off,
@@ -93,26 +96,42 @@ __device__ __forceinline__ uint32_t cell_of(const DevParams &P, double x, double
 // slots come from one atomic per distinct cell of the warp (consecutive
 // particles mostly share a cell), so their order inside a cell is arbitrary;
 // k_reorder restores the id order inside every cell.
-__global__ void k_hash(const double *__restrict__ x, const double *__restrict__ y,
-                       const double *__restrict__ z, int n, DevParams P,
-                       uint32_t *__restrict__ cell_i, uint32_t *__restrict__ slot_i,
-                       uint32_t *__restrict__ count, uint32_t *__restrict__ tile_count,
-                       Scalars *sc)
+__global__ void __launch_bounds__(kHashBlock)
+k_hash(const double *__restrict__ x, const double *__restrict__ y, const double *__restrict__ z,
+       int n, DevParams P, uint32_t *__restrict__ cell_i, uint32_t *__restrict__ slot_i,
+       uint32_t *__restrict__ count, uint32_t *__restrict__ tile_count, Scalars *sc)
 {
+    __shared__ uint32_t tsum[kHashTiles];
+    __shared__ uint32_t tbase;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int lane = threadIdx.x & 31;
     // lanes past the end take a key no particle has, so the warp stays whole
     const uint32_t c = i < n ? cell_of(P, x[i], y[i], z[i]) : 0xffffffffu;
+    if (threadIdx.x < kHashTiles) tsum[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) tbase = i < n ? c / (uint32_t)kScanTile : 0u;
     const unsigned peers = __match_any_sync(0xffffffffu, c);
     const int leader = __ffs(peers) - 1;
     uint32_t base = 0;
     if (i < n && lane == leader) base = atomicAdd(&count[c], (uint32_t)__popc(peers));
     base = __shfl_sync(0xffffffffu, base, leader);
-    // the same count per scan tile of kScanTile cells (the tile sums of the
-    // cell-start scan, so that it needs only its down-sweep)
+    // The same counts per scan tile of kScanTile cells: the tile sums of the
+    // cell-start scan, so that it needs only its down-sweep.  The block's
+    // particles (consecutive in the previous sorted order) lie in a few
+    // consecutive tiles, counted in shared memory from the tile of its first
+    // particle; one global atomic per tile and block (a tile holds tens of
+    // thousands of particles, so per-warp global atomics would queue on a
+    // few addresses).
+    __syncthreads();
     const uint32_t tile = i < n ? c / (uint32_t)kScanTile : 0xffffffffu;
     const unsigned tpeers = __match_any_sync(0xffffffffu, tile);
-    if (i < n && lane == __ffs(tpeers) - 1) atomicAdd(&tile_count[tile], (uint32_t)__popc(tpeers));
+    if (i < n && lane == __ffs(tpeers) - 1) {
+        const uint32_t d = tile - tbase;
+        if (d < (uint32_t)kHashTiles) atomicAdd(&tsum[d], (uint32_t)__popc(tpeers));
+        else atomicAdd(&tile_count[tile], (uint32_t)__popc(tpeers));
+    }
+    __syncthreads();
+    if (threadIdx.x < kHashTiles && tsum[threadIdx.x] != 0u)
+        atomicAdd(&tile_count[tbase + threadIdx.x], tsum[threadIdx.x]);
     if (i < n) {
         cell_i[i] = c;
         slot_i[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
@@ -621,8 +640,8 @@ static int nl_fluid_t(sph_ctx *ctx)
     // cell and slot of every particle (key_tmp, val_tmp), counts per cell and
     // per scan tile
     if (nf > 0)
-        SPH_LAUNCH(ctx, k_hash, (nf + T - 1) / T, T, 0, st, w.x[src], w.y[src], w.z[src], nf,
-                   ctx->dp, w.key_tmp, w.val_tmp, w.count, w.fpart, w.sc);
+        SPH_LAUNCH(ctx, k_hash, (nf + kHashBlock - 1) / kHashBlock, kHashBlock, 0, st, w.x[src],
+                   w.y[src], w.z[src], nf, ctx->dp, w.key_tmp, w.val_tmp, w.count, w.fpart, w.sc);
     int rc = exclusive_scan_down_u32(ctx, w.count, (uint32_t *)w.fstart,
                                      (int64_t)ctx->ncells + 2, w.fpart, st);
     if (rc) return rc;
