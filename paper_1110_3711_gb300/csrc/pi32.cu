@@ -41,17 +41,19 @@
 #include "sph_internal.cuh"
 #include "warp_items.cuh"
 
+// Staged candidates per warp and set.  224 (36.8 KB of shared memory per CTA
+// of 4 warps) admits 6 CTAs, 24 warps, per SM; 256 admitted 5 (PI 2.7 %
+// slower at 1M on GB300).
 #ifndef SPH_PI_CAP
-#define SPH_PI_CAP 256
+#define SPH_PI_CAP 224
 #endif
 #ifndef SPH_PI_WARPS
 #define SPH_PI_WARPS 4
 #endif
-// Resident CTAs per SM the register allocation is held to: shared memory
-// (about 42.7 KB per CTA) admits 5 per SM, and 5 CTAs of 128 threads need at
-// most 96 registers per thread.
+// Resident CTAs per SM the register allocation is held to: 6 CTAs of 128
+// threads need at most 85 registers per thread (the compiler takes 80).
 #ifndef SPH_PI_MINB
-#define SPH_PI_MINB 5
+#define SPH_PI_MINB 6
 #endif
 
 namespace sph {
