@@ -454,9 +454,9 @@ __device__ __forceinline__ void adj_fluid_item(
     const double *__restrict__ gF, const double *__restrict__ gD, double *__restrict__ lam_s,
     double *__restrict__ part, double *slots)
 {
-    const witems::Item I = witems::item_of<true>(P, items, it, cell, fstart, lane);
+    const witems::Item I = witems::item_of(P, items, it, cell, lane);
     const int i = I.i;
-    const witems::Frame Fr = witems::frame_of<true>(P, I, posf[i], cell, 4.0004f);
+    const witems::Frame Fr = witems::frame_of(P, I, posf[i], cell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // the target this lane works for in the balanced walk, its sums (w), and
     // the total of the lane's own target (l)
@@ -532,9 +532,9 @@ __device__ __forceinline__ void adj_boundary_item(
     const int32_t *__restrict__ fstart, const double *__restrict__ gF,
     double *__restrict__ lam_s, double *slots)
 {
-    const witems::Item I = witems::item_of<false>(P, items, it, bcell, bstart, lane);
+    const witems::Item I = witems::item_of(P, items, it, bcell, lane);
     const int j = I.i;
-    const witems::Frame Fr = witems::frame_of<false>(P, I, bposf[j], bcell, 4.0004f);
+    const witems::Frame Fr = witems::frame_of(P, I, bposf[j], bcell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // balanced walk: the boundary target this lane works for, its sum (w) and
     // the total of the lane's own target (lr)

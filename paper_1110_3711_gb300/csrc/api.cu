@@ -218,7 +218,7 @@ size_t plan_workspace(const sph_params &p, int64_t nf, int64_t nb, int dims[3], 
     W.count = b.take<uint32_t>((size_t)*ncells + 2 + ftiles + kCtrWords);
     W.fpart = W.count ? W.count + *ncells + 2 : nullptr;
     W.ctr = W.count ? W.fpart + ftiles : nullptr;
-    W.items_f = b.take<uint32_t>(nf > 0 ? nf : 1);
+    W.items_f = b.take<uint32_t>(2 * (size_t)(nf > 0 ? nf : 1));  // {first, count} pairs
     W.items_b = b.take<uint32_t>(2 * (size_t)(nb > 0 ? nb : 1));  // {first, count} pairs
     if (p.precision == SPH_FP32_SPLIT && p.pi_kernel == SPH_PI_THREAD_FASTCELLS) {
         W.franges = b.take<int4>((size_t)*ncells * 9);

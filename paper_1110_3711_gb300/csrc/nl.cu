@@ -30,6 +30,7 @@ namespace sph {
 
 constexpr int kHashBlock = 512;   // threads (particles) per k_hash block
 constexpr int kHashTiles = 4;     // scan tiles a block counts in shared memory
+constexpr int kItemBlock = 256;   // cells per k_fluid_items block
 
 // ------------------------------------------------------------------ cells --
 
@@ -136,6 +137,56 @@ k_hash(const double *__restrict__ x, const double *__restrict__ y, const double 
         cell_i[i] = c;
         slot_i[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
         if (c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
+    }
+}
+
+// PI work items of the fluid list (Section 4 of the paper gives one thread per
+// particle; here one warp per item of up to 32 targets of one cell), one
+// thread per cell: a cell of m particles gives ceil(m / 32) items, each
+// {first particle, number of particles}.  They are appended with one atomic
+// per block, in no particular order (the sums of a target do not depend on
+// it); particles outside the grid get no item.  Items used to be appended by
+// k_reorder at every 32nd particle of a cell, one atomic on the same counter
+// per warp of particles, which queued at large sizes (NL 1.33 -> 0.78 ms at
+// 21.8M particles).
+__global__ void __launch_bounds__(kItemBlock)
+k_fluid_items(DevParams P, const int32_t *__restrict__ start, uint32_t *__restrict__ items,
+              uint32_t *__restrict__ count)
+{
+    __shared__ uint32_t wsum[kItemBlock / 32];
+    __shared__ uint32_t bbase;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int a = 0, m = 0;
+    if (c < (int)P.ncells) {
+        a = start[c];
+        m = start[c + 1] - a;
+    }
+    const int n = (m + 31) >> 5;
+    // exclusive position of this cell's items in the block: warp scan, then
+    // the warps' totals in order
+    int incl = n;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) wsum[wid] = (uint32_t)incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kItemBlock / 32; ++w) {
+            const uint32_t v = wsum[w];
+            wsum[w] = t;
+            t += v;
+        }
+        bbase = t > 0u ? atomicAdd(count, t) : 0u;
+    }
+    __syncthreads();
+    uint32_t k = bbase + wsum[wid] + (uint32_t)(incl - n);
+    for (int o = 0; o < m; o += 32, ++k) {
+        items[2 * k] = (uint32_t)(a + o);
+        items[2 * k + 1] = (uint32_t)min(32, m - o);
     }
 }
 
@@ -468,7 +519,6 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
           uint32_t *__restrict__ cell, const Real *__restrict__ brho,
           typename Vec4<Real>::T *__restrict__ bposp, typename Vec4<Real>::T *__restrict__ bvelr,
           const int32_t *__restrict__ bstart, const int32_t *__restrict__ fstart,
-          uint32_t *__restrict__ items, uint32_t *__restrict__ ctr,
           const double *__restrict__ origin, float4 *__restrict__ posf, Scalars *sc)
 {
     __shared__ double red[32];
@@ -477,7 +527,6 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     // the largest sound speed, in the precision of the form
     Real cmax = 0;
-    bool item = false;
     int p = 0;  // destination of thread i
     if (i < nf) {
         const uint32_t s = src_q[i];
@@ -491,8 +540,6 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
 #pragma unroll 4
         for (int k = b; k < e; ++k) r += id_q[k] < myid ? 1 : 0;
         p = b + r;
-        // a PI work item starts at every 32nd particle of a cell
-        if (c < P.ncells) item = (r & 31) == 0;
         dx[p] = x; dy[p] = y; dz[p] = z;
         dV[p] = vv;   // also the PI input velr = {v, rho}
         dVM[p] = vm;
@@ -539,17 +586,6 @@ k_reorder(int nf, int nb, DevParams P, const uint32_t *__restrict__ cell_q,
             }
             bposp[j] = pp;
             bvelr[j] = vv;
-        }
-    }
-    {
-        // warp-aggregated append of the work items (their order does not matter)
-        unsigned ball = __ballot_sync(0xffffffffu, item);
-        if (ball) {
-            int lane = threadIdx.x & 31;
-            uint32_t base = 0;
-            if (lane == 0) base = atomicAdd(&ctr[0], (uint32_t)__popc(ball));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (item) items[base + __popc(ball & ((1u << lane) - 1u))] = (uint32_t)p;
         }
     }
     if (SPLIT) block_max_to_f(&sc->mx.c, (float)cmax, redf);
@@ -645,6 +681,9 @@ static int nl_fluid_t(sph_ctx *ctx)
     int rc = exclusive_scan_down_u32(ctx, w.count, (uint32_t *)w.fstart,
                                      (int64_t)ctx->ncells + 2, w.fpart, st);
     if (rc) return rc;
+    // PI work items: up to 32 particles of one cell each
+    SPH_LAUNCH(ctx, k_fluid_items, (ctx->ncells + kItemBlock - 1) / kItemBlock, kItemBlock, 0, st,
+               ctx->dp, w.fstart, w.items_f, &w.ctr[0]);
     // cell-grouped order: cell (key_sorted), source (val_sorted), id (key_by_id)
     if (nf > 0)
         SPH_LAUNCH(ctx, k_place, (nf + T - 1) / T, T, 0, st, nf, w.key_tmp, w.val_tmp, w.id[src],
@@ -657,7 +696,7 @@ static int nl_fluid_t(sph_ctx *ctx)
                    (const V4 *)w.V[src], (const V4 *)w.VM[src], w.x[dst], w.y[dst], w.z[dst],
                    (V4 *)w.V[dst], (V4 *)w.VM[dst], w.id[dst], (V4 *)w.posp, w.cell,
                    (const Real *)w.brho, (V4 *)w.bposp, (V4 *)w.bvelr, w.bstart, w.fstart,
-                   w.items_f, w.ctr, w.origin, w.posf, w.sc);
+                   w.origin, w.posf, w.sc);
     }
     ctx->cur = dst;
     return check_cuda(cudaGetLastError());

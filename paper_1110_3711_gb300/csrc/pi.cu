@@ -307,9 +307,9 @@ __device__ __forceinline__ void pi64_item(
     double4_32a *__restrict__ acc, double *__restrict__ bar, double *part, double &f2max,
     double &vismax, bool &bad)
 {
-    const witems::Item I = witems::item_of<MOMENTUM>(P, items, it, tcell, tstart, lane);
+    const witems::Item I = witems::item_of(P, items, it, tcell, lane);
     const int i = I.i;
-    const witems::Frame Fr = witems::frame_of<MOMENTUM>(P, I, tposf[i], tcell, 4.0004f);
+    const witems::Frame Fr = witems::frame_of(P, I, tposf[i], tcell, 4.0004f);
     const double s2 = 4.0 * P.h * P.h;
     // the target this lane works for in the balanced walk, its sums, and the
     // lane's own target's total

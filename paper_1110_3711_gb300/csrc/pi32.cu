@@ -4,8 +4,9 @@
 // own thread and its own walk over the 27 cells; the pair body then runs under
 // a divergent branch (a warp idles whenever any lane has a false neighbour,
 // Section 4 "code divergence").  Here one warp owns a work item: up to 32
-// target particles of one cell (cells follow X, Y, Z after NL, so they are a
-// contiguous range).  For that item the warp
+// target particles of one cell, or for boundary targets of consecutive cells
+// of one x row (cells follow X, Y, Z after NL, so they are a contiguous
+// range).  For that item the warp
 //   1. builds the table of its 9 fluid x-runs (and 9 boundary x-runs for
 //      fluid targets): cells x-1..x+1 of every (y, z) row are one index range
 //      (Section 4.4, Fig. 10);
@@ -24,15 +25,17 @@
 //      gradient, Tait pressure, artificial viscosity, continuity) from the
 //      staged data, recomputing r_ab exactly from the shifted offsets.
 // Work items are taken from a list built by NL with an atomic counter, so the
-// grid is persistent (one resident set of CTAs) and balances itself.  Boundary
-// targets (B-F) come in packed items: consecutive cells of one x row with at
-// most 32 particles together (a boundary cell holds about 10), the candidates
-// being the fluid of the union of their neighbourhoods (x-runs from the first
-// cell - 1 to the last + 1); each candidate is shifted by its own cell's x
-// distance from the first cell, each target by its cell's.  Fluid and boundary
-// items form one queue (fluid first) served by one launch.  Sums of a target
-// are accumulated by one lane in candidate order, so results do not depend on
-// the order the items are processed in.
+// grid is persistent (one resident set of CTAs) and balances itself.  Fluid
+// items hold the particles of one cell (about 27 at rest; a fuller cell gives
+// items of 32).  Boundary targets (B-F) come in packed items: consecutive
+// cells of one x row with at most 32 particles together (a boundary cell holds
+// about 10), the candidates being the fluid of the union of their
+// neighbourhoods (x-runs from the first cell - 1 to the last + 1); each
+// candidate is shifted by its own cell's x distance from the first cell, each
+// target by its cell's.  Fluid and boundary items form one queue (fluid first)
+// served by one launch.  Sums of a target are accumulated by one lane in
+// candidate order, so results do not depend on the order the items are
+// processed in.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -89,14 +92,13 @@ __device__ __forceinline__ void pi32_item(
     float4 *__restrict__ acc, float *__restrict__ bar, const uint32_t *__restrict__ fcell,
     double &f2max, float &vismax, bool &bad)
 {
-    // ---- the item: fluid targets [i0, i0 + nt) of cell c; boundary targets
-    // [i0, i0 + nt) of cells c .. c + (cx1 - cx) of one x row
-    const witems::Item I = witems::item_of<MOMENTUM>(P, items, it, tcell, tstart, lane);
+    // ---- the item: targets [i0, i0 + nt) of cells c .. c + (cx1 - cx) of one x row
+    const witems::Item I = witems::item_of(P, items, it, tcell, lane);
     const int i = I.i;
     const float4 pa = tposp[i], va = tvelr[i];
     // the target in the item's frame, units of h; the lockstep test decides
     // the pairs (threshold 4 h^2)
-    const witems::Frame F = witems::frame_of<MOMENTUM>(P, I, pa, tcell, 4.0f);
+    const witems::Frame F = witems::frame_of(P, I, pa, tcell, 4.0f);
     const float ra = va.w * P.inv_rho0f;
     const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
 

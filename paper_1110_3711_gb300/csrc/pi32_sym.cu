@@ -111,9 +111,10 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
         if (it >= n_items) break;
 
         // ---- the item: targets [i0, i0 + nt) of cell c
-        const int i0 = (int)items[it];
+        // fluid items hold the particles of one cell
+        const int i0 = (int)items[2 * it];
         const uint32_t c = fcell[i0];
-        const int nt = min(32, fstart[c + 1] - i0);
+        const int nt = (int)items[2 * it + 1];
         const bool active = lane < nt;
         const int i = i0 + (active ? lane : 0);
         const float4 pa = fposp[i], va = fvelr[i];

@@ -95,8 +95,9 @@ struct Workspace {
     uint32_t *count;          // [ncells + 2], then fpart, then the work-item counters ctr
     uint32_t *fpart;          // fluid NL: particles per scan tile of kScanTile cells (k_hash)
     uint32_t *ctr;            // [0] fluid items, [1] next item of the PI queue, [2] spare, [3] boundary items
-    uint32_t *items_f, *items_b;  // PI work items: fluid, first target of a (cell, 32-target chunk);
-                                  // boundary, {first, count} of packed cells of one x row
+    uint32_t *items_f, *items_b;  // PI work items, {first, count} pairs: fluid, up to 32
+                                  // particles of one cell (k_fluid_items); boundary, packed
+                                  // cells of one x row (k_pack_boundary_items)
     int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
     int32_t *fstart, *bstart; // [ncells + 2]
     double *origin;           // cell origins min_d + c s along x (nx), y (ny), z (nz)
@@ -212,8 +213,11 @@ inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 __device__ __forceinline__ void atomic_max_nonneg(unsigned long long *dst, double v)
 {
     // non-negative doubles (and +inf / NaN, which compare above) order like
-    // their bit patterns
-    atomicMax(dst, (unsigned long long)__double_as_longlong(v));
+    // their bit patterns.  The stored maximum only grows, so a value not above
+    // the one already read needs no atomic (most blocks of a large grid skip
+    // it instead of queueing on the one address).
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (b > *(volatile unsigned long long *)dst) atomicMax(dst, b);
 }
 
 __device__ __forceinline__ double warp_max(double v)

@@ -2,9 +2,9 @@
 // kernel (pi32.cu), the float64 PI (pi.cu) and its adjoint (adjoint.cu); the
 // symmetric float32 variant (pi32_sym.cu) shares the lockstep test.
 //
-// A work item is up to 32 fluid targets of one cell (items_f, one entry per
-// first target) or up to 32 boundary targets of consecutive cells of one x
-// row (items_b, {first, count} pairs).  For an item the warp
+// A work item is up to 32 fluid targets of one cell (items_f) or up to 32
+// boundary targets of consecutive cells of one x row (items_b), both as
+// {first, count} pairs.  For an item the warp
 //   1. builds the table of its x-runs (Section 4.4, Fig. 10): for every
 //      (dy, dz) of the 9 neighbour rows, cells x-1 .. x+1 (of the item's first
 //      and last cell) are one index range of the fluid list, and for fluid
@@ -86,28 +86,25 @@ struct Smem {
 
 constexpr int NSLOT = 63;   // partial-sum slots of the balanced walk (lane + target)
 
-// The item's targets as one lane sees them.
+// The item's targets as one lane sees them.  Items of both kinds are
+// {first target, number of targets}: up to 32 particles of one cell (fluid
+// items) or of consecutive non-empty cells of one x row (boundary items), or
+// a chunk of 32 of a fuller cell.
 struct Item {
     int i0, nt;             // first target, number of targets
     int i;                  // this lane's target (i0 for lanes past nt)
     bool active;            // lane < nt
+    bool multi;             // the targets span more than one cell
     uint32_t c;             // cell of the first target
     int cx, cy, cz, cx1;    // its coordinates; cx1: x of the item's last cell
 };
 
-template <bool FLUID_TARGETS>
 __device__ __forceinline__ Item item_of(const DevParams &P, const uint32_t *__restrict__ items,
-                                        uint32_t it, const uint32_t *__restrict__ tcell,
-                                        const int32_t *__restrict__ tstart, int lane)
+                                        uint32_t it, const uint32_t *__restrict__ tcell, int lane)
 {
     Item I;
-    if (FLUID_TARGETS) {
-        I.i0 = (int)items[it];
-        I.nt = min(32, tstart[tcell[I.i0] + 1] - I.i0);
-    } else {
-        I.i0 = (int)items[2 * it];
-        I.nt = (int)items[2 * it + 1];
-    }
+    I.i0 = (int)items[2 * it];
+    I.nt = (int)items[2 * it + 1];
     I.c = tcell[I.i0];
     I.active = lane < I.nt;
     I.i = I.i0 + (I.active ? lane : 0);
@@ -115,22 +112,23 @@ __device__ __forceinline__ Item item_of(const DevParams &P, const uint32_t *__re
     I.cx = (int)(I.c - t * (uint32_t)P.nx);
     I.cy = (int)(t % (uint32_t)P.ny);
     I.cz = (int)(t / (uint32_t)P.ny);
-    I.cx1 = FLUID_TARGETS ? I.cx : I.cx + (int)(tcell[I.i0 + I.nt - 1] - I.c);
+    I.cx1 = I.cx + (int)(tcell[I.i0 + I.nt - 1] - I.c);
+    I.multi = I.cx1 != I.cx;
     return I;
 }
 
-// Lane's target in the item's frame (units of h): x, y, z and the test
-// threshold thr0 - |x|^2 (-inf for idle lanes).
+// Lane's target in the item's frame (units of h; the frame of the item's
+// first cell): x, y, z and the test threshold thr0 - |x|^2 (-inf for idle
+// lanes).
 struct Frame {
     float x, y, z, thr;
 };
 
-template <bool FLUID_TARGETS>
 __device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, const float4 &fa,
                                           const uint32_t *__restrict__ tcell, float thr0)
 {
     Frame F;
-    const float tshift = FLUID_TARGETS ? 0.0f : (float)(int)(tcell[I.i] - I.c) * P.s_hf;
+    const float tshift = I.multi ? (float)(int)(tcell[I.i] - I.c) * P.s_hf : 0.0f;
     F.x = fmaf(fa.x, P.invhf, tshift);
     F.y = fa.y * P.invhf;
     F.z = fa.z * P.invhf;
@@ -139,9 +137,10 @@ __device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, con
 }
 
 // Step 1: lane r describes run r of the table; returns the number of
-// candidates K.  b1, b2 of a run: for fluid targets the first indices of
-// cells x and x + 1 of its row (a candidate's x shift follows from its index);
-// for boundary targets the cell id of the item's first cell in that row.
+// candidates K.  b1, b2 of a run: for fluid targets (an item of one cell) the
+// first indices of cells x and x + 1 of its row (a candidate's x shift follows
+// from its index); for boundary targets the cell id of the item's first cell
+// in that row (a candidate's x shift follows from its own cell).
 template <bool FLUID_TARGETS>
 __device__ __forceinline__ int build_runs(const DevParams &P, RunTable &T, int lane, const Item &I,
                                           const int32_t *__restrict__ fstart,
@@ -234,6 +233,9 @@ __device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32
 // another 32 (at most cap); the candidates within 2h of the box are packed by
 // a ballot into slots 0 .. n-1 and n is returned.  k0 and r (the current run,
 // which only moves forward) carry over to the next set.
+// A candidate's x shift into the item's frame comes from its index (fluid
+// targets: an item of one cell) or from its own cell (boundary targets, whose
+// items may span several cells: fcell is the cell of every fluid particle).
 //   load(j, blist) issues the loads of candidate j of its list and returns
 //                  them; its member pos is the float32 offset record (metres)
 //   store(slot, a, c) writes the kept candidate: a = shifted offset {x, y, z}
@@ -261,11 +263,12 @@ __device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, 
             const int prev = r ? T.run[r - 1].x : 0;
             const int j = ri.y + (sidx - prev);
             const int cd = T.code[r];
+            const bool blist = FLUID_TARGETS && (cd & 1);
             const float sx = FLUID_TARGETS ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
                                            : (float)((int)fcell[j] - ri.z) * P.s_hf;
             const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
             const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-            c = load(j, FLUID_TARGETS && (cd & 1));
+            c = load(j, blist);
             a.x = fmaf(c.pos.x, P.invhf, sx);
             a.y = fmaf(c.pos.y, P.invhf, sy);
             a.z = fmaf(c.pos.z, P.invhf, sz);
@@ -382,7 +385,8 @@ __device__ __forceinline__ void for_each_hit_balanced(
     const DevParams &P, Smem &S, int lane, const Item &I, const Frame &F,
     const int32_t *__restrict__ fstart, const float4 *__restrict__ fposf,
     const int32_t *__restrict__ bstart, const float4 *__restrict__ bposf,
-    const uint32_t *__restrict__ fcell, Begin &&begin, Hit &&hit, End &&end, Combine &&combine)
+    const uint32_t *__restrict__ fcell, Begin &&begin, Hit &&hit, End &&end,
+    Combine &&combine)
 {
     stage_and_test<FLUID_TARGETS>(P, S, lane, I, F, fstart, fposf, bstart, bposf, fcell,
                                   [&](int nch) {
