@@ -5,10 +5,11 @@
 //                 id cx + nx (cy + ny cz) (cells follow X, Y, Z; Section 4.4),
 //                 the per-cell counts and a slot inside the cell (atomics),
 //                 and the counts per scan tile of kScanTile cells.
-//   cell starts   exclusive scan of the per-cell counts: start[c] = number of
+//   k_scan_items  exclusive scan of the per-cell counts: start[c] = number of
 //                 particles in cells below c, i.e. CellBeginEnd of Fig. 8 with
 //                 empty cells as equal begin and end; its tile sums come from
-//                 k_hash, so the scan is one down-sweep kernel.
+//                 k_hash, so the scan is one down-sweep; the same kernel
+//                 appends the PI work items of the cells it scans.
 //   k_place       cell-grouped order start[c] + slot (arbitrary inside a cell).
 //   k_reorder     rank by id inside the cell, which gives the (cell, id) order
 //                 whatever the order before; copy of the fluid state (x, y, z
@@ -30,7 +31,6 @@ namespace sph {
 
 constexpr int kHashBlock = 512;   // threads (particles) per k_hash block
 constexpr int kHashTiles = 4;     // scan tiles a block counts in shared memory
-constexpr int kItemBlock = 256;   // cells per k_fluid_items block
 
 // ------------------------------------------------------------------ cells --
 
@@ -137,56 +137,6 @@ k_hash(const double *__restrict__ x, const double *__restrict__ y, const double 
         cell_i[i] = c;
         slot_i[i] = base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
         if (c == P.ncells) atomicOr(&sc->flags, SPH_FLAG_OUT_OF_GRID);
-    }
-}
-
-// PI work items of the fluid list (Section 4 of the paper gives one thread per
-// particle; here one warp per item of up to 32 targets of one cell), one
-// thread per cell: a cell of m particles gives ceil(m / 32) items, each
-// {first particle, number of particles}.  They are appended with one atomic
-// per block, in no particular order (the sums of a target do not depend on
-// it); particles outside the grid get no item.  Items used to be appended by
-// k_reorder at every 32nd particle of a cell, one atomic on the same counter
-// per warp of particles, which queued at large sizes (NL 1.33 -> 0.78 ms at
-// 21.8M particles).
-__global__ void __launch_bounds__(kItemBlock)
-k_fluid_items(DevParams P, const int32_t *__restrict__ start, uint32_t *__restrict__ items,
-              uint32_t *__restrict__ count)
-{
-    __shared__ uint32_t wsum[kItemBlock / 32];
-    __shared__ uint32_t bbase;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int a = 0, m = 0;
-    if (c < (int)P.ncells) {
-        a = start[c];
-        m = start[c + 1] - a;
-    }
-    const int n = (m + 31) >> 5;
-    // exclusive position of this cell's items in the block: warp scan, then
-    // the warps' totals in order
-    int incl = n;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) wsum[wid] = (uint32_t)incl;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        uint32_t t = 0;
-        for (int w = 0; w < kItemBlock / 32; ++w) {
-            const uint32_t v = wsum[w];
-            wsum[w] = t;
-            t += v;
-        }
-        bbase = t > 0u ? atomicAdd(count, t) : 0u;
-    }
-    __syncthreads();
-    uint32_t k = bbase + wsum[wid] + (uint32_t)(incl - n);
-    for (int o = 0; o < m; o += 32, ++k) {
-        items[2 * k] = (uint32_t)(a + o);
-        items[2 * k + 1] = (uint32_t)min(32, m - o);
     }
 }
 
@@ -377,16 +327,69 @@ k_scan_down(const uint32_t *in, uint32_t *out, int64_t n, const uint32_t *__rest
     }
 }
 
-size_t scan_partials(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
-
-int exclusive_scan_down_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
-                            const uint32_t *partials, cudaStream_t st)
+// The down-sweep of k_scan_down over the fluid cell counts (start = the cell
+// starts, n = ncells + 2 entries), which also appends the PI work items of
+// the fluid list: a cell of m particles (c < ncells; the particles outside the
+// grid get none) gives ceil(m / 32) items {first particle, number of
+// particles} of up to 32 targets of that cell (the paper's GPU kernel gives
+// one thread per particle, Section 4; here one warp per item).  The items of
+// a block are appended with one atomic, so their order between blocks is
+// arbitrary (the sums of a target do not depend on it).
+__global__ void __launch_bounds__(kScanBlock)
+k_scan_items(const uint32_t *count, uint32_t *start, int64_t n, const uint32_t *__restrict__ part,
+             uint32_t ncells, uint32_t *__restrict__ items, uint32_t *__restrict__ n_items)
 {
-    if (n <= 0) return SPH_OK;
-    const int64_t blocks = scan_tiles(n);
-    SPH_LAUNCH(ctx, k_scan_down, (unsigned)blocks, kScanBlock, 0, st, in, out, n, partials);
-    return check_cuda(cudaGetLastError());
+    __shared__ uint32_t smem[33];
+    __shared__ uint32_t base_s, ibase_s;
+    uint32_t b = 0;
+    for (int k = threadIdx.x; k < (int)blockIdx.x; k += kScanBlock) b += part[k];
+    for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
+    if ((threadIdx.x & 31) == 0) smem[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < kScanBlock / 32; ++w) t += smem[w];
+        base_s = t;
+    }
+    __syncthreads();
+    const int64_t c0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    uint32_t v[kScanItems];
+    uint32_t s = 0, ni = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        v[k] = c0 + k < n ? count[c0 + k] : 0u;
+        s += v[k];
+        if (c0 + k < (int64_t)ncells) ni += (v[k] + 31u) >> 5;
+    }
+    const uint32_t ex0 = block_exclusive(s, smem) + base_s;
+    uint32_t ex = ex0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (c0 + k < n) start[c0 + k] = ex;
+        ex += v[k];
+    }
+    // the block's items: exclusive position of this thread's, then one atomic
+    uint32_t it = block_exclusive(ni, smem);
+    if (threadIdx.x == kScanBlock - 1) {
+        const uint32_t tot = it + ni;
+        ibase_s = tot ? atomicAdd(n_items, tot) : 0u;
+    }
+    __syncthreads();
+    it += ibase_s;
+    ex = ex0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+        if (c0 + k < (int64_t)ncells) {
+            for (uint32_t o = 0; o < v[k]; o += 32u, ++it) {
+                items[2 * (size_t)it] = ex + o;
+                items[2 * (size_t)it + 1] = min(32u, v[k] - o);
+            }
+        }
+        ex += v[k];
+    }
 }
+
+size_t scan_partials(int64_t n) { return (size_t)((n + kScanTile - 1) / kScanTile) + 1; }
 
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *partials, cudaStream_t st)
@@ -678,12 +681,10 @@ static int nl_fluid_t(sph_ctx *ctx)
     if (nf > 0)
         SPH_LAUNCH(ctx, k_hash, (nf + kHashBlock - 1) / kHashBlock, kHashBlock, 0, st, w.x[src],
                    w.y[src], w.z[src], nf, ctx->dp, w.key_tmp, w.val_tmp, w.count, w.fpart, w.sc);
-    int rc = exclusive_scan_down_u32(ctx, w.count, (uint32_t *)w.fstart,
-                                     (int64_t)ctx->ncells + 2, w.fpart, st);
-    if (rc) return rc;
-    // PI work items: up to 32 particles of one cell each
-    SPH_LAUNCH(ctx, k_fluid_items, (ctx->ncells + kItemBlock - 1) / kItemBlock, kItemBlock, 0, st,
-               ctx->dp, w.fstart, w.items_f, &w.ctr[0]);
+    // cell starts and the PI work items (up to 32 particles of one cell each)
+    SPH_LAUNCH(ctx, k_scan_items, (unsigned)ftiles, kScanBlock, 0, st, w.count,
+               (uint32_t *)w.fstart, (int64_t)ctx->ncells + 2, w.fpart, ctx->ncells, w.items_f,
+               &w.ctr[0]);
     // cell-grouped order: cell (key_sorted), source (val_sorted), id (key_by_id)
     if (nf > 0)
         SPH_LAUNCH(ctx, k_place, (nf + T - 1) / T, T, 0, st, nf, w.key_tmp, w.val_tmp, w.id[src],

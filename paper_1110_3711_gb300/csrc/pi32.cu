@@ -74,7 +74,7 @@ struct WarpSmem {
     float4 V[CAP];        // candidate {vx, vy, vz, rho}
     float Pr[CAP];        // candidate P / rho^2
     uint32_t M[NCH][32];  // hit bits of lane l for chunk q
-    witems::RunTable T;   // x-runs and the targets' bounding box
+    witems::RunTable T;   // x-runs
 };
 
 // One work item, processed by the whole warp.  MOMENTUM: fluid targets (F-F
@@ -103,7 +103,7 @@ __device__ __forceinline__ void pi32_item(
     const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
 
     const int K = witems::build_runs<MOMENTUM>(P, S.T, lane, I, fstart, bstart);
-    witems::target_box(S.T, lane, F);
+    const witems::Box B = witems::target_box(F);
 
     // staged data of a kept candidate: offset (A, from the position record),
     // {v, rho} (V) and P/rho^2 (Pr); both loads are issued together (the
@@ -134,8 +134,8 @@ __device__ __forceinline__ void pi32_item(
         const int np = witems::pass_slots(K, npass, pass);
         int k0 = 0, r = 0;
         while (k0 < np) {
-            const int n = witems::stage_set<MOMENTUM>(P, S.T, lane, CAP, pass, npass, np, K, k0,
-                                                      r, fcell, load, store);
+            const int n = witems::stage_set<MOMENTUM>(P, S.T, B, lane, CAP, pass, npass, np, K,
+                                                      k0, r, fcell, load, store);
             // far candidates fill the last chunk
             const int nch = (n + 31) >> 5;
             if (n + lane < nch * 32) {
@@ -145,12 +145,13 @@ __device__ __forceinline__ void pi32_item(
             }
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
-            witems::lockstep_tests(S.A, S.M, nch, lane, F);
+            witems::lockstep_tests<true>(S.A, S.M, n, lane, F);
             // |x|^2 has served the tests: the pair walk reads P/rho^2 from its place
             __syncwarp();
             for (int q2 = 0; q2 < nch; ++q2) S.A[q2 * 32 + lane].w = S.Pr[q2 * 32 + lane];
             __syncwarp();
-            // ---- every lane walks its own hits (about 112 per lane in all)
+            // ---- every lane walks its own hits (about 112 per lane in all), in
+            // staging order: candidate k of chunk q is bit 31 - k of its mask
             int q = 0;
             uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
             for (;;) {
@@ -159,8 +160,9 @@ __device__ __forceinline__ void pi32_item(
                     m = S.M[q][lane];
                 }
                 if (m == 0u) break;
-                const int ls = q * 32 + __ffs(m) - 1;
-                m &= m - 1u;
+                const int k = __clz(m);
+                m &= 0x7fffffffu >> k;
+                const int ls = q * 32 + k;
                 const float4 b = S.A[ls];
                 pair_acc32<MOMENTUM, TENSILE>(P, F.x - b.x, F.y - b.y, F.z - b.z, pa.w, va, cpa,
                                               S.V[ls], b.w, o);

@@ -231,7 +231,7 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
             }
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
-            witems::lockstep_tests(S.A, S.M, nch, lane, witems::Frame{xa, ya, za, thr});
+            witems::lockstep_tests<false>(S.A, S.M, np, lane, witems::Frame{xa, ya, za, thr});
             // ---- every lane walks its own hits; b-side terms to the candidate's
             // slot.  All lanes iterate together (until no lane has a hit left)
             // so that the warp-wide match below is well defined.

@@ -96,7 +96,7 @@ struct Workspace {
     uint32_t *fpart;          // fluid NL: particles per scan tile of kScanTile cells (k_hash)
     uint32_t *ctr;            // [0] fluid items, [1] next item of the PI queue, [2] spare, [3] boundary items
     uint32_t *items_f, *items_b;  // PI work items, {first, count} pairs: fluid, up to 32
-                                  // particles of one cell (k_fluid_items); boundary, packed
+                                  // particles of one cell (k_scan_items); boundary, packed
                                   // cells of one x row (k_pack_boundary_items)
     int4 *franges, *branges;      // per-cell x-run tables (SPH_PI_THREAD_FASTCELLS)
     int32_t *fstart, *bstart; // [ncells + 2]
@@ -203,10 +203,6 @@ constexpr int kScanTile = kScanBlock * kScanItems;
 
 int exclusive_scan_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
                        uint32_t *partials, cudaStream_t st);
-// The down-sweep of exclusive_scan_u32 alone, for tile sums (partials) the
-// caller has already formed.
-int exclusive_scan_down_u32(sph_ctx *ctx, const uint32_t *in, uint32_t *out, int64_t n,
-                            const uint32_t *partials, cudaStream_t st);
 // Tiles of kScanTile entries in a scan of n entries.
 inline int64_t scan_tiles(int64_t n) { return (n + kScanTile - 1) / kScanTile; }
 

@@ -68,11 +68,20 @@ __device__ __forceinline__ int pass_candidate(int ls, int npass, int pass)
 // distance and of the lockstep test, so that no hit of either form is lost.
 constexpr float BOX_THR = 4.0004f;
 
-// The item's x-runs and its targets' bounding box.
+// A candidate sampled by a pass is a block of BLK consecutive ones, and the
+// 32 lanes of a staging round take 32 consecutive sample slots.
+static_assert(32 % BLK == 0, "a staging round must hold whole pass blocks");
+
+// The item's x-runs.
 struct RunTable {
-    int4 run[NRUN];         // {inclusive end slot, first index, b1, b2}
-    int code[NRUN];         // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4)
-    float box[6];           // targets' bounding box: min x, max x, min y, max y, min z, max z
+    int4 run[NRUN];         // {inclusive end slot, first index - first slot, b1, b2}
+    float2 sh[NRUN];        // y and z shift of the run's row into the item frame (units of h)
+};
+
+// The bounding box of the item's targets: centre and half extent along x, y, z
+// (units of h, item frame), the same in every lane.
+struct Box {
+    float cx, ex, cy, ey, cz, ez;
 };
 
 // Staged candidates of the float64 kernels.
@@ -81,6 +90,7 @@ struct Smem {
     uint32_t J[CAP];        // candidate index, bit 31 set for the boundary list
     uint32_t M[NCH][32];    // hit bits of lane l for chunk q
     RunTable T;
+    Box B;                  // the targets' box (kept here, not in registers, during the walks)
     int hincl[32];          // balanced walk: hits of targets 0 .. t of the tested set
 };
 
@@ -148,12 +158,12 @@ __device__ __forceinline__ int build_runs(const DevParams &P, RunTable &T, int l
 {
     const int nlists = FLUID_TARGETS ? 2 : 1;
     const int r = lane;
-    int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
+    int L = 0, j0 = 0, b1 = 0, b2 = 0, dy = 0, dz = 0;
     if (r < 9 * nlists) {
         const int list = r / 9, q = r % 9;
-        const int dz = q / 3 - 1, dy = q % 3 - 1;
+        dz = q / 3 - 1;
+        dy = q % 3 - 1;
         const int y = I.cy + dy, z = I.cz + dz;
-        code = list | ((dy + 1) << 1) | ((dz + 1) << 3);
         if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
             const int32_t *st = list ? bstart : fstart;
             const int row = P.nx * (y + P.ny * z);
@@ -175,16 +185,18 @@ __device__ __forceinline__ int build_runs(const DevParams &P, RunTable &T, int l
         if (lane >= o) pe += t;
     }
     if (r < NRUN) {
-        T.run[r] = make_int4(pe, j0, b1, b2);
-        T.code[r] = code;
+        // candidate at sample index sidx of this run: index sidx + (j0 - first slot)
+        T.run[r] = make_int4(pe, j0 - (pe - L), b1, b2);
+        T.sh[r] = make_float2((float)dy * P.s_hf, (float)dz * P.s_hf);
     }
     const int K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
     __syncwarp();
     return K;
 }
 
-// The bounding box of the item's active targets (units of h, item frame).
-__device__ __forceinline__ void target_box(RunTable &T, int lane, const Frame &F)
+// The bounding box of the item's active targets, reduced over the warp so that
+// every lane holds it.
+__device__ __forceinline__ Box target_box(const Frame &F)
 {
     const bool act = F.thr > -INFINITY;
     float b[6] = {act ? F.x : INFINITY, act ? F.x : -INFINITY, act ? F.y : INFINITY,
@@ -197,34 +209,50 @@ __device__ __forceinline__ void target_box(RunTable &T, int lane, const Frame &F
             b[2 * d + 1] = fmaxf(b[2 * d + 1], __shfl_xor_sync(0xffffffffu, b[2 * d + 1], o));
         }
     }
-    if (lane == 0) {
-#pragma unroll
-        for (int d = 0; d < 6; ++d) T.box[d] = b[d];
-    }
-    __syncwarp();
+    Box B;
+    B.cx = 0.5f * (b[0] + b[1]);
+    B.ex = 0.5f * (b[1] - b[0]);
+    B.cy = 0.5f * (b[2] + b[3]);
+    B.ey = 0.5f * (b[3] - b[2]);
+    B.cz = 0.5f * (b[4] + b[5]);
+    B.ez = 0.5f * (b[5] - b[4]);
+    return B;
 }
 
-// Step 3 for the nch chunks of 32 staged candidates in A (their w is |x|^2):
-// bit k of M[q][lane] is set when candidate q * 32 + k is a hit of this
-// lane's target.  The sign of t - thr is shifted into two independent
-// 16-candidate masks (candidate k lands at bit 15 - k of its half), which are
-// joined and bit-reversed so that candidate k ends at bit k.
-__device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32], int nch,
+// Step 3 for the n staged candidates in A (their w is |x|^2; slots n .. of the
+// last chunk hold far candidates): bit k of M[q][lane] (MSB_FIRST: bit 31 - k)
+// is set when candidate q * 32 + k is a hit of this lane's target.  The sign
+// of t - thr is shifted into two independent 16-candidate masks (candidate k
+// lands at bit 15 - k of its half), which are joined (and bit-reversed unless
+// MSB_FIRST).  A last chunk of at most 16 candidates tests one half.
+template <bool MSB_FIRST>
+__device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32], int n,
                                                int lane, const Frame &F)
 {
     const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
+    const int nch = (n + 31) >> 5;
     for (int q = 0; q < nch; ++q) {
         uint32_t lo = 0u, hi = 0u;
+        if (n - 32 * q > 16) {
 #pragma unroll
-        for (int k = 0; k < 16; ++k) {
-            const float4 a = A[q * 32 + k];
-            const float4 b = A[q * 32 + 16 + k];
-            const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
-            const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
-            lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
-            hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+            for (int k = 0; k < 16; ++k) {
+                const float4 a = A[q * 32 + k];
+                const float4 b = A[q * 32 + 16 + k];
+                const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
+                const float tb = fmaf(m2x, b.x, fmaf(m2y, b.y, fmaf(m2z, b.z, b.w))) - F.thr;
+                lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+                hi = __funnelshift_l(__float_as_uint(tb), hi, 1);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) {
+                const float4 a = A[q * 32 + k];
+                const float ta = fmaf(m2x, a.x, fmaf(m2y, a.y, fmaf(m2z, a.z, a.w))) - F.thr;
+                lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
+            }
         }
-        M[q][lane] = __brev((lo << 16) | hi);
+        const uint32_t w = (lo << 16) | hi;
+        M[q][lane] = MSB_FIRST ? w : __brev(w);
     }
 }
 
@@ -241,40 +269,39 @@ __device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32
 //   store(slot, a, c) writes the kept candidate: a = shifted offset {x, y, z}
 //                  in units of h and |x|^2, c what load returned
 template <bool FLUID_TARGETS, class Load, class Store>
-__device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, int lane, int cap,
-                                         int pass, int npass, int np, int K, int &k0, int &r,
-                                         const uint32_t *__restrict__ fcell, Load &&load,
-                                         Store &&store)
+__device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, const Box &Bx,
+                                         int lane, int cap, int pass, int npass, int np, int K,
+                                         int &k0, int &r, const uint32_t *__restrict__ fcell,
+                                         Load &&load, Store &&store)
 {
     typedef decltype(load(0, false)) Cand;
-    // the box is uniform over the warp: held in registers for the whole set
-    const float bx0 = T.box[0], bx1 = T.box[1], by0 = T.box[2], by1 = T.box[3],
-                bz0 = T.box[4], bz1 = T.box[5];
+    // the box is uniform over the warp: held in registers for the set
+    const Box B = Bx;
+    // sample index of slot k0 + lane: rounds of 32 slots hold whole blocks, so
+    // it advances by 32 npass per round
+    int sidx = pass_candidate(lane, npass, pass) + k0 * npass;
     int n = 0;
     while (k0 < np && n <= cap - 32) {
         const int ls = k0 + lane;
-        const int sidx = pass_candidate(ls, npass, pass);
         bool keep = false;
         float4 a;
         Cand c;
         if (ls < np && sidx < K) {
             while (sidx >= T.run[r].x) ++r;
             const int4 ri = T.run[r];
-            const int prev = r ? T.run[r - 1].x : 0;
-            const int j = ri.y + (sidx - prev);
-            const int cd = T.code[r];
-            const bool blist = FLUID_TARGETS && (cd & 1);
+            const int j = sidx + ri.y;
+            const float2 sh = T.sh[r];
+            const bool blist = FLUID_TARGETS && r >= 9;
             const float sx = FLUID_TARGETS ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
                                            : (float)((int)fcell[j] - ri.z) * P.s_hf;
-            const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-            const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
             c = load(j, blist);
             a.x = fmaf(c.pos.x, P.invhf, sx);
-            a.y = fmaf(c.pos.y, P.invhf, sy);
-            a.z = fmaf(c.pos.z, P.invhf, sz);
-            const float dx = fmaxf(fmaxf(bx0 - a.x, a.x - bx1), 0.0f);
-            const float dy = fmaxf(fmaxf(by0 - a.y, a.y - by1), 0.0f);
-            const float dz = fmaxf(fmaxf(bz0 - a.z, a.z - bz1), 0.0f);
+            a.y = fmaf(c.pos.y, P.invhf, sh.x);
+            a.z = fmaf(c.pos.z, P.invhf, sh.y);
+            // distance to the box along each axis: |a - centre| - half extent, or 0 inside
+            const float dx = fmaxf(fabsf(a.x - B.cx) - B.ex, 0.0f);
+            const float dy = fmaxf(fabsf(a.y - B.cy) - B.ey, 0.0f);
+            const float dz = fmaxf(fabsf(a.z - B.cz) - B.ez, 0.0f);
             keep = fmaf(dx, dx, fmaf(dy, dy, dz * dz)) < BOX_THR;
             if (keep) a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
         }
@@ -282,6 +309,7 @@ __device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, 
         if (keep) store(n + __popc(ball & ((1u << lane) - 1u)), a, c);
         n += __popc(ball);
         k0 += 32;
+        sidx += 32 * npass;
     }
     return n;
 }
@@ -301,7 +329,11 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
                                                const uint32_t *__restrict__ fcell, Flush &&flush)
 {
     const int K = build_runs<FLUID_TARGETS>(P, S.T, lane, I, fstart, bstart);
-    target_box(S.T, lane, F);
+    {
+        const Box B = target_box(F);
+        if (lane == 0) S.B = B;
+        __syncwarp();
+    }
     struct Cand {
         float4 pos;
         uint32_t jj;
@@ -321,8 +353,8 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
         const int np = pass_slots(K, npass, pass);
         int k0 = 0, r = 0;
         while (k0 < np) {
-            const int n = stage_set<FLUID_TARGETS>(P, S.T, lane, CAP, pass, npass, np, K, k0, r,
-                                                   fcell, load, store);
+            const int n = stage_set<FLUID_TARGETS>(P, S.T, S.B, lane, CAP, pass, npass, np, K,
+                                                   k0, r, fcell, load, store);
             // far candidates fill the last chunk
             const int nch = (n + 31) >> 5;
             if (n + lane < nch * 32) {
@@ -330,7 +362,7 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
                 S.J[n + lane] = 0u;
             }
             __syncwarp();
-            lockstep_tests(S.A, S.M, nch, lane, F);
+            lockstep_tests<false>(S.A, S.M, n, lane, F);
             __syncwarp();
             flush(nch);
             __syncwarp();

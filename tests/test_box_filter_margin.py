@@ -3,7 +3,9 @@ lockstep test can report as a hit.
 
 The kernels (float32, units of h, item frame) keep a candidate b when
     d2 = fma(dx, dx, fma(dy, dy, dz * dz)) < 4.0004,
-    dx = max(box_x0 - b_x, b_x - box_x1, 0)   (same for y, z),
+    dx = max(|b_x - c_x| - e_x, 0)   (same for y, z),
+with the box's centre c_x = (box_x0 + box_x1) / 2 and half extent
+e_x = (box_x1 - box_x0) / 2, each rounded to float32,
 and the lockstep test reports a hit of target a when
     fma(-2 a_x, b_x, fma(-2 a_y, b_y, fma(-2 a_z, b_z, |b|^2))) - (4 - |a|^2) < 0.
 A target lies inside the box, so |a - b| >= distance(b, box); the test below
@@ -30,20 +32,24 @@ def hits(ax, ay, az, bx, by, bz):
     return (t - thr) < 0
 
 
-def kept(box, bx, by, bz):
-    dx = np.maximum(np.maximum(box[0] - bx, bx - box[1]), F(0.0))
-    dy = np.maximum(np.maximum(box[2] - by, by - box[3]), F(0.0))
-    dz = np.maximum(np.maximum(box[4] - bz, bz - box[5]), F(0.0))
-    return fma32(dx, dx, fma32(dy, dy, dz * dz)) < F(4.0004)
+def kept(box, bx, by, bz, thr=F(4.0004)):
+    d = []
+    for k, b in enumerate((bx, by, bz)):
+        lo, hi = F(box[2 * k]), F(box[2 * k + 1])
+        c = F(0.5) * (lo + hi)
+        e = F(0.5) * (hi - lo)
+        d.append(np.maximum(np.abs(b - c) - e, F(0.0)))
+    dx, dy, dz = d
+    return fma32(dx, dx, fma32(dy, dy, dz * dz)) < thr
 
 
-def _check(targets, cands):
+def _check(targets, cands, thr=F(4.0004)):
     ax, ay, az = (targets[:, k][:, None] for k in range(3))
     bx, by, bz = (cands[:, k][None, :] for k in range(3))
     box = [targets[:, 0].min(), targets[:, 0].max(), targets[:, 1].min(),
            targets[:, 1].max(), targets[:, 2].min(), targets[:, 2].max()]
     h = hits(ax, ay, az, bx, by, bz)
-    k = kept(box, cands[:, 0], cands[:, 1], cands[:, 2])
+    k = kept(box, cands[:, 0], cands[:, 1], cands[:, 2], thr)
     assert not np.any(h & ~k[None, :]), "a hit was dropped by the box filter"
     return int(h.sum()), int(k.sum())
 
@@ -72,3 +78,18 @@ def test_candidates_on_the_support_sphere_lose_no_hit():
         cands = (a + r * u).astype(F)
         nh, _ = _check(targets, cands)
         assert nh > 0
+
+
+def test_margin_is_needed():
+    # a threshold below the support radius drops hits of candidates on the
+    # support sphere, so the check above can fail
+    rng = np.random.default_rng(2)
+    targets = rng.uniform(0.0, 2.0, size=(1, 3)).astype(F)
+    u = rng.normal(size=(4000, 3))
+    u /= np.linalg.norm(u, axis=1)[:, None]
+    cands = (targets[0].astype(np.float64) + 1.99999 * u).astype(F)
+    try:
+        _check(targets, cands, thr=F(3.9999))
+    except AssertionError:
+        return
+    raise AssertionError("a threshold of 3.9999 kept every hit")
