@@ -111,7 +111,7 @@ __device__ __forceinline__ void pi32_item(
     struct Cand {
         float4 pos, v;
     };
-    auto load = [&](int j, bool blist) {
+    auto load = [&](int j, bool blist, bool) {
         Cand c;
         c.pos = blist ? bposp[j] : fposp[j];
         c.v = blist ? bvelr[j] : fvelr[j];

@@ -22,14 +22,17 @@
 //   boundary:  all 9 rows, evaluated for both particles (the B-F continuity
 //              term of a boundary particle is the b side of an F-B pair), so no
 //              separate boundary-target kernel runs.
-// The lockstep distance test (warp_items.cuh) and the per-lane hit walk are those of
-// the warp kernel, in units of h with the constants folded out of the loop.
-// The b-side terms of a pass are summed per staged candidate in shared memory
+// The work-item search is that of the warp kernel (warp_items.cuh: run table
+// with the half-shell runs, candidates within 2h of the targets' bounding box
+// staged in passes of 8-candidate blocks, lockstep distance tests), and the
+// per-lane hit walk and pair terms are those of the warp kernel, in units of h
+// with the constants folded out of the loop.
+// The b-side terms of a staged set are summed per candidate in shared memory
 // (lanes that reach the same candidate in the same iteration take turns, the
 // turn decided by the last lane id written to the slot's tag; shared-memory
 // float atomics cost more than the pairs they save), then every candidate with
-// a non-zero
-// sum adds it to the particle's global sums with one vector atomic; the a-side
+// a non-zero sum adds it to the particle's global sums with one vector atomic;
+// the a-side
 // sums of the targets are added the same way at the end of the item.  The
 // global sums start at (g, 0) (k_sym_init) and the largest |a|^2 is taken after
 // the kernel (k_sym_max).
@@ -49,24 +52,28 @@ namespace sph {
 
 namespace {
 
-constexpr int CAP = 160;          // staged candidates per warp and pass
+constexpr int CAP = 160;          // staged candidates per warp and set
 constexpr int NCH = CAP / 32;
 constexpr int WARPS = 4;
-constexpr int NRUN = 14;          // 5 fluid + 9 boundary x-runs
+constexpr int RAW_PER_PASS = 2 * CAP;  // candidates sampled per pass (before the box test)
 static_assert(CAP % 32 == 0, "CAP must be a multiple of 32");
+
+// Staged candidate index flags: boundary list, evaluated for both particles.
+constexpr uint32_t J_BOUNDARY = 0x80000000u;
+constexpr uint32_t J_BOTH = 0x40000000u;
+constexpr uint32_t J_INDEX = 0x3fffffffu;
 
 struct WarpSmem {
     float4 A[CAP];        // shifted candidate offset {x, y, z} / h and |x|^2
     float4 V[CAP];        // candidate {vx, vy, vz, rho}
-    float4 B[CAP];        // b-side sums of the pass: (-f r'), (v.r') F''
+    float4 B[CAP];        // b-side sums of the set: (-f r'), (v.r') F''
     float Pr[CAP];        // candidate P / rho^2
-    int J[CAP];           // candidate index in its list
+    uint32_t J[CAP];      // candidate index and its J_ flags
     int tag[CAP];         // lane allowed to add to the slot in the current round
     uint32_t M[NCH][32];  // hit bits of lane l for chunk q
     uint32_t symF[NCH];   // fluid candidates evaluated for both particles
     uint32_t isB[NCH];    // boundary candidates (always both particles)
-    int4 run[NRUN];       // {inclusive end slot, first index, start of cell x, start of cell x+1}
-    int code[NRUN];       // list (bit 0), dy+1 (bits 1-2), dz+1 (bits 3-4), own row (bit 5)
+    witems::RunTable T;   // the half-shell x-runs
 };
 
 __device__ __forceinline__ void red_add_v4(float4 *p, float a, float b, float c, float d)
@@ -110,201 +117,145 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
         it = __shfl_sync(0xffffffffu, it, 0);
         if (it >= n_items) break;
 
-        // ---- the item: targets [i0, i0 + nt) of cell c
-        // fluid items hold the particles of one cell
-        const int i0 = (int)items[2 * it];
-        const uint32_t c = fcell[i0];
-        const int nt = (int)items[2 * it + 1];
-        const bool active = lane < nt;
-        const int i = i0 + (active ? lane : 0);
+        // ---- the item: the targets of one cell (fluid items hold one cell)
+        const witems::Item I = witems::item_of(P, items, it, fcell, lane);
+        const int i = I.i;
         const float4 pa = fposp[i], va = fvelr[i];
-        const uint32_t cyz = c / (uint32_t)P.nx;
-        const int cx = (int)(c - cyz * (uint32_t)P.nx);
-        const int cy = (int)(cyz % (uint32_t)P.ny);
-        const int cz = (int)(cyz / (uint32_t)P.ny);
-        const float xa = pa.x * P.invhf, ya = pa.y * P.invhf, za = pa.z * P.invhf;
-        const float thr = active ? 4.0f - fmaf(xa, xa, fmaf(ya, ya, za * za)) : -INFINITY;
+        const witems::Frame F = witems::frame_of(P, I, pa, fcell, 4.0f);
         const float ra = va.w * P.inv_rho0f;
         const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
+        const int K = witems::build_runs<true, witems::RUNS_HALF>(P, S.T, lane, I, fstart, bstart);
+        const witems::Box Bx = witems::target_box(F);
 
-        // ---- run table: lane r describes run r
-        int K;
-        {
-            const int r = lane;
-            int L = 0, j0 = 0, b1 = 0, b2 = 0, code = 0;
-            if (r < NRUN) {
-                int list, dy, dz, x0, x1;
-                if (r < 5) {
-                    // fluid: rows (-1, +1), (0, +1), (+1, +1), (+1, 0) whole,
-                    // and cells x, x+1 of the own row
-                    list = 0;
-                    dy = r < 3 ? r - 1 : (r == 3 ? 1 : 0);
-                    dz = r < 3 ? 1 : 0;
-                    x0 = r == 4 ? cx : max(cx - 1, 0);
-                } else {
-                    list = 1;
-                    dz = (r - 5) / 3 - 1;
-                    dy = (r - 5) % 3 - 1;
-                    x0 = max(cx - 1, 0);
-                }
-                x1 = min(cx + 1, P.nx - 1);
-                const int y = cy + dy, z = cz + dz;
-                code = list | ((dy + 1) << 1) | ((dz + 1) << 3) | (r == 4 ? 32 : 0);
-                if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
-                    const int32_t *st = list ? bstart : fstart;
-                    const int row = P.nx * (y + P.ny * z);
-                    j0 = st[row + x0];
-                    L = st[row + x1 + 1] - j0;
-                    b1 = st[row + cx];
-                    b2 = st[row + cx + 1];
-                }
-            }
-            int pe = L;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, pe, o);
-                if (lane >= o) pe += t;
-            }
-            if (r < NRUN) {
-                S.run[r] = make_int4(pe, j0, b1, b2);
-                S.code[r] = code;
-            }
-            K = __shfl_sync(0xffffffffu, pe, NRUN - 1);
-        }
-        __syncwarp();
+        struct Cand {
+            float4 pos, v;
+            uint32_t jj;
+        };
+        auto load = [&](int j, bool blist, bool own) {
+            Cand c;
+            c.pos = blist ? bposp[j] : fposp[j];
+            c.v = blist ? bvelr[j] : fvelr[j];
+            // own row: the target cell is one-sided, cell x+1 symmetric
+            c.jj = (uint32_t)j | (blist ? J_BOUNDARY : (own ? 0u : J_BOTH));
+            return c;
+        };
+        auto store = [&](int slot, const float4 &a, const Cand &c) {
+            S.A[slot] = a;
+            S.V[slot] = c.v;
+            S.Pr[slot] = c.pos.w;
+            S.J[slot] = c.jj;
+            S.B[slot] = make_float4(0.f, 0.f, 0.f, 0.f);
+        };
 
         float ax = 0.f, ay = 0.f, az = 0.f, ar = 0.f;
-        const int npass = (K + CAP - 1) / CAP;
+        const int npass = (K + RAW_PER_PASS - 1) / RAW_PER_PASS;
         for (int pass = 0; pass < npass; ++pass) {
-            const int np = (K - pass + npass - 1) / npass;
-            const int nch = (np + 31) >> 5;
-            // ---- stage the candidates of this pass (pass p takes p, p + npass, ...)
-            int r = 0;
-            for (int m = 0; m < nch; ++m) {
-                const int ls = lane + 32 * m;
-                const int s = ls < np ? pass + npass * ls : K;
-                float4 a, v;
-                float pr;
-                int j = 0;
-                bool symf = false, isb = false;
-                if (s < K) {
-                    while (s >= S.run[r].x) ++r;
-                    const int4 ri = S.run[r];
-                    const int prev = r ? S.run[r - 1].x : 0;
-                    j = ri.y + (s - prev);
-                    const int cd = S.code[r];
-                    const float sx = j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf);
-                    const float sy = (float)(((cd >> 1) & 3) - 1) * P.s_hf;
-                    const float sz = (float)(((cd >> 3) & 3) - 1) * P.s_hf;
-                    float4 p;
-                    if (cd & 1) {
-                        p = bposp[j];
-                        v = bvelr[j];
-                        isb = true;
-                    } else {
-                        p = fposp[j];
-                        v = fvelr[j];
-                        // own row: the target cell is one-sided, cell x+1 symmetric
-                        symf = !(cd & 32) || j >= ri.w;
-                    }
-                    a.x = fmaf(p.x, P.invhf, sx);
-                    a.y = fmaf(p.y, P.invhf, sy);
-                    a.z = fmaf(p.z, P.invhf, sz);
-                    a.w = fmaf(a.x, a.x, fmaf(a.y, a.y, a.z * a.z));
-                    pr = p.w;
-                } else {
-                    a = make_float4(0.f, 0.f, 0.f, INFINITY);
-                    v = make_float4(0.f, 0.f, 0.f, 1.f);
-                    pr = 0.f;
+            const int np = witems::pass_slots(K, npass, pass);
+            int k0 = 0, r = 0;
+            while (k0 < np) {
+                const int n = witems::stage_set<true, witems::RUNS_HALF>(
+                    P, S.T, Bx, lane, CAP, pass, npass, np, K, k0, r, fcell, load, store);
+                // far candidates fill the last chunk
+                const int nch = (n + 31) >> 5;
+                if (n + lane < nch * 32) {
+                    S.A[n + lane] = make_float4(0.f, 0.f, 0.f, INFINITY);
+                    S.V[n + lane] = make_float4(0.f, 0.f, 0.f, 1.f);
+                    S.Pr[n + lane] = 0.f;
+                    S.J[n + lane] = 0u;
+                    S.B[n + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                S.A[ls] = a;
-                S.V[ls] = v;
-                S.Pr[ls] = pr;
-                S.J[ls] = j;
-                S.B[ls] = make_float4(0.f, 0.f, 0.f, 0.f);
-                const uint32_t bf = __ballot_sync(0xffffffffu, symf);
-                const uint32_t bb = __ballot_sync(0xffffffffu, isb);
-                if (lane == 0) {
-                    S.symF[m] = bf;
-                    S.isB[m] = bb;
-                }
-            }
-            __syncwarp();
-            // ---- lockstep distance tests, one hit bit per candidate
-            witems::lockstep_tests<false>(S.A, S.M, np, lane, witems::Frame{xa, ya, za, thr});
-            // ---- every lane walks its own hits; b-side terms to the candidate's
-            // slot.  All lanes iterate together (until no lane has a hit left)
-            // so that the warp-wide match below is well defined.
-            int q = 0;
-            uint32_t m = S.M[0][lane], sf = S.symF[0], sb = S.isB[0];
-            for (;;) {
-                while (m == 0u && q + 1 < nch) {
-                    ++q;
-                    m = S.M[q][lane];
-                    sf = S.symF[q];
-                    sb = S.isB[q];
-                }
-                const bool has = m != 0u;
-                if (!__any_sync(0xffffffffu, has)) break;
-                int ls = 0;
-                bool two = false;
-                float4 add = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (has) {
-                    const int bit = __ffs(m) - 1;
-                    m &= m - 1u;
-                    ls = q * 32 + bit;
-                    const float4 b = S.A[ls];
-                    const float rx = xa - b.x, ry = ya - b.y, rz = za - b.z;
-                    float coef, cF;
-                    pair_sym(P, rx, ry, rz, pa.w, va, cpa, S.V[ls], S.Pr[ls], coef, cF, vismax);
-                    ax = fmaf(coef, rx, ax);
-                    ay = fmaf(coef, ry, ay);
-                    az = fmaf(coef, rz, az);
-                    ar += cF;
-                    if ((sf >> bit) & 1u) {
-                        two = true;
-                        add = make_float4(-coef * rx, -coef * ry, -coef * rz, cF);
-                    } else if ((sb >> bit) & 1u) {
-                        two = true;
-                        add.w = cF;
+                __syncwarp();
+                for (int q = 0; q < nch; ++q) {
+                    const uint32_t jj = S.J[q * 32 + lane];
+                    const uint32_t bf = __ballot_sync(0xffffffffu, (jj & J_BOTH) != 0u);
+                    const uint32_t bb = __ballot_sync(0xffffffffu, (jj & J_BOUNDARY) != 0u);
+                    if (lane == 0) {
+                        S.symF[q] = bf;
+                        S.isB[q] = bb;
                     }
                 }
-                // lanes that reached the same candidate take turns: each lane
-                // with something to add writes its id to the slot's tag, and
-                // the lane whose id is read back adds; the others try again
-                bool todo = two;
-                while (__any_sync(0xffffffffu, todo)) {
-                    if (todo) S.tag[ls] = lane;
-                    __syncwarp();
-                    const bool mine = todo && S.tag[ls] == lane;
-                    if (mine) {
-                        float4 t = S.B[ls];
-                        t.x += add.x;
-                        t.y += add.y;
-                        t.z += add.z;
-                        t.w += add.w;
-                        S.B[ls] = t;
-                        todo = false;
+                __syncwarp();
+                // ---- lockstep distance tests, one hit bit per candidate
+                witems::lockstep_tests<false>(S.A, S.M, n, lane, F);
+                __syncwarp();
+                // ---- every lane walks its own hits; b-side terms to the candidate's
+                // slot.  All lanes iterate together (until no lane has a hit left)
+                // so that the warp-wide turns below are well defined.
+                int q = 0;
+                uint32_t m = nch > 0 ? S.M[0][lane] : 0u, sf = nch > 0 ? S.symF[0] : 0u,
+                         sb = nch > 0 ? S.isB[0] : 0u;
+                for (;;) {
+                    while (m == 0u && q + 1 < nch) {
+                        ++q;
+                        m = S.M[q][lane];
+                        sf = S.symF[q];
+                        sb = S.isB[q];
                     }
-                    __syncwarp();
+                    const bool has = m != 0u;
+                    if (!__any_sync(0xffffffffu, has)) break;
+                    int ls = 0;
+                    bool two = false;
+                    float4 add = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (has) {
+                        const int bit = __ffs(m) - 1;
+                        m &= m - 1u;
+                        ls = q * 32 + bit;
+                        const float4 b = S.A[ls];
+                        const float rx = F.x - b.x, ry = F.y - b.y, rz = F.z - b.z;
+                        float coef, cF;
+                        pair_sym(P, rx, ry, rz, pa.w, va, cpa, S.V[ls], S.Pr[ls], coef, cF,
+                                 vismax);
+                        ax = fmaf(coef, rx, ax);
+                        ay = fmaf(coef, ry, ay);
+                        az = fmaf(coef, rz, az);
+                        ar += cF;
+                        if ((sf >> bit) & 1u) {
+                            two = true;
+                            add = make_float4(-coef * rx, -coef * ry, -coef * rz, cF);
+                        } else if ((sb >> bit) & 1u) {
+                            two = true;
+                            add.w = cF;
+                        }
+                    }
+                    // lanes that reached the same candidate take turns: each lane
+                    // with something to add writes its id to the slot's tag, and
+                    // the lane whose id is read back adds; the others try again
+                    bool todo = two;
+                    while (__any_sync(0xffffffffu, todo)) {
+                        if (todo) S.tag[ls] = lane;
+                        __syncwarp();
+                        const bool mine = todo && S.tag[ls] == lane;
+                        if (mine) {
+                            float4 t = S.B[ls];
+                            t.x += add.x;
+                            t.y += add.y;
+                            t.z += add.z;
+                            t.w += add.w;
+                            S.B[ls] = t;
+                            todo = false;
+                        }
+                        __syncwarp();
+                    }
                 }
-            }
-            __syncwarp();
-            // ---- b-side sums of the pass to the particles
-            for (int mm = 0; mm < nch; ++mm) {
-                const int ls = lane + 32 * mm;
-                const float4 bs = S.B[ls];
-                if ((S.symF[mm] >> lane) & 1u) {
-                    if (bs.x != 0.f || bs.y != 0.f || bs.z != 0.f || bs.w != 0.f)
-                        red_add_v4(acc + S.J[ls], P.nmkBf * bs.x, P.nmkBf * bs.y, P.nmkBf * bs.z,
-                                   P.mkBf * bs.w);
-                } else if ((S.isB[mm] >> lane) & 1u) {
-                    if (bs.w != 0.f) atomicAdd(bar + S.J[ls], P.mkBf * bs.w);
+                __syncwarp();
+                // ---- b-side sums of the set to the particles
+                for (int mm = 0; mm < nch; ++mm) {
+                    const int ls = lane + 32 * mm;
+                    const float4 bs = S.B[ls];
+                    const uint32_t jj = S.J[ls];
+                    const uint32_t j = jj & J_INDEX;
+                    if (jj & J_BOTH) {
+                        if (bs.x != 0.f || bs.y != 0.f || bs.z != 0.f || bs.w != 0.f)
+                            red_add_v4(acc + j, P.nmkBf * bs.x, P.nmkBf * bs.y, P.nmkBf * bs.z,
+                                       P.mkBf * bs.w);
+                    } else if (jj & J_BOUNDARY) {
+                        if (bs.w != 0.f) atomicAdd(bar + j, P.mkBf * bs.w);
+                    }
                 }
+                __syncwarp();
             }
-            __syncwarp();
         }
-        if (active) red_add_v4(acc + i, P.nmkBf * ax, P.nmkBf * ay, P.nmkBf * az, P.mkBf * ar);
+        if (I.active) red_add_v4(acc + i, P.nmkBf * ax, P.nmkBf * ay, P.nmkBf * az, P.mkBf * ar);
     }
     block_max_to(&sc->mx.visc, (double)vismax, red);
 }

@@ -146,28 +146,55 @@ __device__ __forceinline__ Frame frame_of(const DevParams &P, const Item &I, con
     return F;
 }
 
+// Which x-runs an item searches.  RUNS_FULL: the 9 (dy, dz) rows of the fluid
+// list (runs 0-8) and, for fluid targets, of the boundary list (runs 9-17),
+// cells x-1 .. x+1 each.  RUNS_HALF (fluid targets of one cell, symmetric pair
+// evaluation): the fluid cells after the item's own cell in (z, y, x) order,
+// i.e. the rows (dy, dz) = (-1, +1), (0, +1), (+1, +1), (+1, 0) whole (runs
+// 0-3) and cells x, x+1 of the own row (run 4), then the 9 boundary rows
+// (runs 5-13).
+constexpr int RUNS_FULL = 0;
+constexpr int RUNS_HALF = 1;
+
+// First run of the boundary list.
+template <bool FLUID_TARGETS, int RUNS>
+__device__ __forceinline__ constexpr int first_boundary_run()
+{
+    return !FLUID_TARGETS ? NRUN : (RUNS == RUNS_HALF ? 5 : 9);
+}
+
 // Step 1: lane r describes run r of the table; returns the number of
 // candidates K.  b1, b2 of a run: for fluid targets (an item of one cell) the
 // first indices of cells x and x + 1 of its row (a candidate's x shift follows
 // from its index); for boundary targets the cell id of the item's first cell
 // in that row (a candidate's x shift follows from its own cell).
-template <bool FLUID_TARGETS>
+template <bool FLUID_TARGETS, int RUNS = RUNS_FULL>
 __device__ __forceinline__ int build_runs(const DevParams &P, RunTable &T, int lane, const Item &I,
                                           const int32_t *__restrict__ fstart,
                                           const int32_t *__restrict__ bstart)
 {
-    const int nlists = FLUID_TARGETS ? 2 : 1;
+    static_assert(RUNS == RUNS_FULL || FLUID_TARGETS, "half-shell runs need fluid targets");
+    const int nruns = RUNS == RUNS_HALF ? 14 : (FLUID_TARGETS ? 18 : 9);
     const int r = lane;
     int L = 0, j0 = 0, b1 = 0, b2 = 0, dy = 0, dz = 0;
-    if (r < 9 * nlists) {
-        const int list = r / 9, q = r % 9;
-        dz = q / 3 - 1;
-        dy = q % 3 - 1;
+    if (r < nruns) {
+        const int fb = first_boundary_run<FLUID_TARGETS, RUNS>();
+        const int list = r >= fb ? 1 : 0;
+        int x0off = -1;
+        if (RUNS == RUNS_HALF && !list) {
+            dz = r < 3 ? 1 : 0;
+            dy = r < 3 ? r - 1 : (r == 3 ? 1 : 0);
+            if (r == 4) x0off = 0;
+        } else {
+            const int q = list ? r - fb : r;
+            dz = q / 3 - 1;
+            dy = q % 3 - 1;
+        }
         const int y = I.cy + dy, z = I.cz + dz;
         if (y >= 0 && y < P.ny && z >= 0 && z < P.nz) {
             const int32_t *st = list ? bstart : fstart;
             const int row = P.nx * (y + P.ny * z);
-            const int x0 = max(I.cx - 1, 0), x1 = min(I.cx1 + 1, P.nx - 1);
+            const int x0 = max(I.cx + x0off, 0), x1 = min(I.cx1 + 1, P.nx - 1);
             j0 = st[row + x0];
             L = st[row + x1 + 1] - j0;
             if (FLUID_TARGETS) {
@@ -264,17 +291,19 @@ __device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32
 // A candidate's x shift into the item's frame comes from its index (fluid
 // targets: an item of one cell) or from its own cell (boundary targets, whose
 // items may span several cells: fcell is the cell of every fluid particle).
-//   load(j, blist) issues the loads of candidate j of its list and returns
-//                  them; its member pos is the float32 offset record (metres)
+//   load(j, blist, own) issues the loads of candidate j of its list and
+//                  returns them; its member pos is the float32 offset record
+//                  (metres); own: a candidate of the item's own cell in the
+//                  RUNS_HALF search (evaluated for the target side only)
 //   store(slot, a, c) writes the kept candidate: a = shifted offset {x, y, z}
 //                  in units of h and |x|^2, c what load returned
-template <bool FLUID_TARGETS, class Load, class Store>
+template <bool FLUID_TARGETS, int RUNS = RUNS_FULL, class Load, class Store>
 __device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, const Box &Bx,
                                          int lane, int cap, int pass, int npass, int np, int K,
                                          int &k0, int &r, const uint32_t *__restrict__ fcell,
                                          Load &&load, Store &&store)
 {
-    typedef decltype(load(0, false)) Cand;
+    typedef decltype(load(0, false, false)) Cand;
     // the box is uniform over the warp: held in registers for the set
     const Box B = Bx;
     // sample index of slot k0 + lane: rounds of 32 slots hold whole blocks, so
@@ -291,10 +320,11 @@ __device__ __forceinline__ int stage_set(const DevParams &P, const RunTable &T, 
             const int4 ri = T.run[r];
             const int j = sidx + ri.y;
             const float2 sh = T.sh[r];
-            const bool blist = FLUID_TARGETS && r >= 9;
+            const bool blist = r >= first_boundary_run<FLUID_TARGETS, RUNS>();
+            const bool own = RUNS == RUNS_HALF && r == 4 && j < ri.w;
             const float sx = FLUID_TARGETS ? (j < ri.z ? -P.s_hf : (j < ri.w ? 0.0f : P.s_hf))
                                            : (float)((int)fcell[j] - ri.z) * P.s_hf;
-            c = load(j, blist);
+            c = load(j, blist, own);
             a.x = fmaf(c.pos.x, P.invhf, sx);
             a.y = fmaf(c.pos.y, P.invhf, sh.x);
             a.z = fmaf(c.pos.z, P.invhf, sh.y);
@@ -338,7 +368,7 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
         float4 pos;
         uint32_t jj;
     };
-    auto load = [&](int j, bool blist) {
+    auto load = [&](int j, bool blist, bool) {
         Cand c;
         c.pos = blist ? bposf[j] : fposf[j];
         c.jj = (uint32_t)j | (blist ? 0x80000000u : 0u);
