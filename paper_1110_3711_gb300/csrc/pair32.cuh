@@ -13,9 +13,12 @@
 //   viscosity:    mu_ab = h v_ab.r_ab / (r^2 + eta^2)        =  v_ab.r' / (q^2 + eta^2/h^2)
 //   Pi_ab = -alpha (c_a + c_b) mu_ab / (rho_a + rho_b)  for mu_ab < 0, else 0.
 // The kernels sum (...) F'' r' and (v_ab . r') F'' and apply the constant
-// factors -m kB and m kB once per target.  cpa = -alpha c_a is a per-target
-// constant; -alpha c_b is kcf rho_b^3 (Tait sound speed with gamma = 7,
-// c = c0 (rho / rho0)^3).
+// factors -m kB and m kB once per target.  The float32 form needs gamma = 7,
+// whose Tait sound speed is c = c0 (rho / rho0)^3; with
+// a^3 + b^3 = (a + b)(a^2 - a b + b^2) the viscosity factor is
+//   -alpha (c_a + c_b) / (rho_a + rho_b) = kcf (rho_a^2 - rho_a rho_b + rho_b^2),
+// kcf = -alpha c0 / rho0^3, so the pair needs no reciprocal of rho_a + rho_b;
+// rho2a = rho_a^2 is a per-target constant.
 #pragma once
 
 #include "sph_internal.cuh"
@@ -24,8 +27,8 @@ namespace sph {
 
 // Approximate reciprocal and reciprocal square root (PTX rcp.approx and
 // rsqrt.approx, relative error about 2^-23).  Their arguments in the pair
-// terms are normal numbers (densities, r'^2 + eta^2/h^2 >= eta^2/h^2, r'^2
-// clamped at 1e-30), so flushing subnormals changes nothing.
+// terms are normal numbers (r'^2 + eta^2/h^2 >= eta^2/h^2, r'^2 + 1e-30), so
+// flushing subnormals changes nothing.
 __device__ __forceinline__ float rcp_approx(float x)
 {
     float y;
@@ -63,15 +66,17 @@ __device__ __forceinline__ float tensile32(const DevParams &P, float q, float pr
 //   coef = (P_a/rho_a^2 + P_b/rho_b^2 + Pi_ab [+ T_ab]) F''   (MOMENTUM only)
 //   vdr  = v_ab . r',  F = F''  (the continuity term is vdr F)
 // and vis = max(vis, |mu_ab|).  pra, prb: P/rho^2 of a and b; va, vb:
-// {vx, vy, vz, rho}.
+// {vx, vy, vz, rho}; rho2a = rho_a^2.
 template <bool MOMENTUM, bool TENSILE>
 __device__ __forceinline__ void pair_terms32(const DevParams &P, float rx, float ry, float rz,
-                                             float pra, const float4 &va, float cpa,
+                                             float pra, const float4 &va, float rho2a,
                                              const float4 &vb, float prb, float &coef,
                                              float &vdr_out, float &F_out, float &vis)
 {
-    const float r2 = fmaf(rx, rx, fmaf(ry, ry, rz * rz));
-    const float rinv = rsqrt_approx(fmaxf(r2, 1e-30f));
+    // 1e-30 keeps the reciprocal square root finite for r = 0 (the pair a = a,
+    // whose terms vanish with r'); for r'^2 of the pairs it is far below rounding
+    const float r2 = fmaf(rx, rx, fmaf(ry, ry, fmaf(rz, rz, 1e-30f)));
+    const float rinv = rsqrt_approx(r2);
     const float q = r2 * rinv;
     const float t = 2.0f - q;
     const float F = q < 1.0f ? fmaf(P.gw1, q, P.gw0) : t * t * rinv;
@@ -79,13 +84,14 @@ __device__ __forceinline__ void pair_terms32(const DevParams &P, float rx, float
     const float vdr = fmaf(dvx, rx, fmaf(dvy, ry, dvz * rz));
     const float mu = vdr * rcp_approx(r2 + P.eta2_h2f);
     if (MOMENTUM) {
-        const float cc = fmaf(P.kcf, vb.w * vb.w * vb.w, cpa);
+        // rho_b^2 - rho_a rho_b + rho_a^2; rho_b - rho_a is exact (two densities
+        // within a factor of two of each other)
+        const float kq = P.kcf * fmaf(vb.w, vb.w - va.w, rho2a);
         if (TENSILE) {
-            const float Pi = cc * fminf(mu, 0.0f) * rcp_approx(va.w + vb.w) +
-                             tensile32(P, q, pra, prb);
+            const float Pi = kq * fminf(mu, 0.0f) + tensile32(P, q, pra, prb);
             coef = (pra + prb + Pi) * F;
         } else {
-            coef = fmaf(cc * fminf(mu, 0.0f), rcp_approx(va.w + vb.w), pra + prb) * F;
+            coef = fmaf(kq, fminf(mu, 0.0f), pra + prb) * F;
         }
     }
     vdr_out = vdr;
@@ -96,11 +102,11 @@ __device__ __forceinline__ void pair_terms32(const DevParams &P, float rx, float
 // pair_terms32 accumulated into the sums of target a.
 template <bool MOMENTUM, bool TENSILE>
 __device__ __forceinline__ void pair_acc32(const DevParams &P, float rx, float ry, float rz,
-                                           float pra, const float4 &va, float cpa,
+                                           float pra, const float4 &va, float rho2a,
                                            const float4 &vb, float prb, Acc32 &o)
 {
     float coef = 0.0f, vdr, F;
-    pair_terms32<MOMENTUM, TENSILE>(P, rx, ry, rz, pra, va, cpa, vb, prb, coef, vdr, F, o.vis);
+    pair_terms32<MOMENTUM, TENSILE>(P, rx, ry, rz, pra, va, rho2a, vb, prb, coef, vdr, F, o.vis);
     if (MOMENTUM) {
         o.ax = fmaf(coef, rx, o.ax);
         o.ay = fmaf(coef, ry, o.ay);

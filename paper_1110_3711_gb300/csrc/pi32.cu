@@ -99,8 +99,7 @@ __device__ __forceinline__ void pi32_item(
     // the target in the item's frame, units of h; the lockstep test decides
     // the pairs (threshold 4 h^2)
     const witems::Frame F = witems::frame_of(P, I, pa, tcell, 4.0f);
-    const float ra = va.w * P.inv_rho0f;
-    const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
+    const float rho2a = va.w * va.w;
 
     const int K = witems::build_runs<MOMENTUM>(P, S.T, lane, I, fstart, bstart);
     const witems::Box B = witems::target_box(F);
@@ -164,7 +163,7 @@ __device__ __forceinline__ void pi32_item(
                 m &= 0x7fffffffu >> k;
                 const int ls = q * 32 + k;
                 const float4 b = S.A[ls];
-                pair_acc32<MOMENTUM, TENSILE>(P, F.x - b.x, F.y - b.y, F.z - b.z, pa.w, va, cpa,
+                pair_acc32<MOMENTUM, TENSILE>(P, F.x - b.x, F.y - b.y, F.z - b.z, pa.w, va, rho2a,
                                               S.V[ls], b.w, o);
             }
             __syncwarp();

@@ -88,11 +88,11 @@ __device__ __forceinline__ void red_add_v4(float4 *p, float a, float b, float c,
 // term of a is -m kB f'' r', that of b +m kB f'' r'; both continuity terms are
 // m kB (v.r') F''.
 __device__ __forceinline__ void pair_sym(const DevParams &P, float rx, float ry, float rz,
-                                         float pra, const float4 &va, float cpa, const float4 &vb,
+                                         float pra, const float4 &va, float rho2a, const float4 &vb,
                                          float prb, float &coef, float &cF, float &vis)
 {
     float vdr, F;
-    pair_terms32<true, false>(P, rx, ry, rz, pra, va, cpa, vb, prb, coef, vdr, F, vis);
+    pair_terms32<true, false>(P, rx, ry, rz, pra, va, rho2a, vb, prb, coef, vdr, F, vis);
     cF = vdr * F;
 }
 
@@ -122,8 +122,7 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
         const int i = I.i;
         const float4 pa = fposp[i], va = fvelr[i];
         const witems::Frame F = witems::frame_of(P, I, pa, fcell, 4.0f);
-        const float ra = va.w * P.inv_rho0f;
-        const float cpa = P.nalphaf * (P.c0f * ra * ra * ra);
+        const float rho2a = va.w * va.w;
         const int K = witems::build_runs<true, witems::RUNS_HALF>(P, S.T, lane, I, fstart, bstart);
         const witems::Box Bx = witems::target_box(F);
 
@@ -203,7 +202,7 @@ k_pi32_sym(DevParams P, const uint32_t *__restrict__ items, const uint32_t *__re
                         const float4 b = S.A[ls];
                         const float rx = F.x - b.x, ry = F.y - b.y, rz = F.z - b.z;
                         float coef, cF;
-                        pair_sym(P, rx, ry, rz, pa.w, va, cpa, S.V[ls], S.Pr[ls], coef, cF,
+                        pair_sym(P, rx, ry, rz, pa.w, va, rho2a, S.V[ls], S.Pr[ls], coef, cF,
                                  vismax);
                         ax = fmaf(coef, rx, ax);
                         ay = fmaf(coef, ry, ay);

@@ -22,13 +22,13 @@ namespace sph {
 namespace {
 
 // The pair terms of the warp kernel (pair32.cuh, units of h) for r_ab in
-// metres; cpa = -alpha c_a.
+// metres; rho2a = rho_a^2.
 template <bool MOMENTUM>
 __device__ __forceinline__ void pair_t(const DevParams &P, const float4 &pa, const float4 &va,
-                                       float cpa, const float4 &pb, const float4 &vb, float rx,
+                                       float rho2a, const float4 &pb, const float4 &vb, float rx,
                                        float ry, float rz, Acc32 &o)
 {
-    pair_acc32<MOMENTUM, false>(P, rx * P.invhf, ry * P.invhf, rz * P.invhf, pa.w, va, cpa, vb,
+    pair_acc32<MOMENTUM, false>(P, rx * P.invhf, ry * P.invhf, rz * P.invhf, pa.w, va, rho2a, vb,
                                 pb.w, o);
 }
 
@@ -111,8 +111,7 @@ k_pi_thread_fluid(int nf, DevParams P, const float4 *__restrict__ posp,
         const uint32_t t = c / (uint32_t)P.nx;
         const int cx = (int)(c - t * (uint32_t)P.nx), cy = (int)(t % (uint32_t)P.ny),
                   cz = (int)(t / (uint32_t)P.ny);
-        const float ra = va.w * P.inv_rho0f;
-        const float ca = P.nalphaf * (P.c0f * ra * ra * ra);  // -alpha c_a
+        const float ca = va.w * va.w;  // rho_a^2
         Acc32 o = {0.f, 0.f, 0.f, 0.f, 0.f};
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, posp, velr, fstart, franges, o);
         runs_t<true, FAST, R>(P, pa, va, ca, c, cx, cy, cz, bposp, bvelr, bstart, branges, o);
