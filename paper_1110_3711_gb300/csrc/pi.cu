@@ -17,6 +17,7 @@
 //   grad_a W_ab = F r_ab,  F = aD/h^2 (-3 + 2.25 q)         (q < 1)
 //                            = -0.75 aD/h (2 - q)^2 / r       (1 <= q < 2), aD = 1/(pi h^3)
 //   mu = h v_ab.r_ab / (r^2 + eta^2);  Pi = -alpha (c_a + c_b) mu / (rho_a + rho_b) if v_ab.r_ab < 0
+//     (gamma = 7: -alpha (c_a + c_b)/(rho_a + rho_b) = -alpha c0/rho0^3 (rho_a^2 - rho_a rho_b + rho_b^2))
 //   ace_a += -m (P_a/rho_a^2 + P_b/rho_b^2 + Pi) F r_ab      (fluid targets)
 //   ar_a  +=  m F v_ab.r_ab
 //   visc   = max(visc, |mu|)
@@ -77,15 +78,24 @@ __device__ __forceinline__ void pair64(const DevParams &P, const double4_32a &pa
     double vdr = dvx * rx + dvy * ry + dvz * rz;
     double mu;
     if (MOMENTUM) {
-        // one reciprocal for both quotients: d = 1/((r^2 + eta^2)(rho_a + rho_b))
-        const double S = va.w + vb.w, hv = P.h * vdr;
-        const double d = 1.0 / ((r2 + P.eta2) * S);
-        mu = hv * S * d;
         double Pi = 0.0;
-        if (vdr < 0.0) {
-            double rb = vb.w * P.inv_rho0;
-            double cb = P.gamma_is_7 ? P.c0 * rb * rb * rb : P.c0 * pow(rb, 0.5 * (P.gamma - 1.0));
-            Pi = -P.alpha * (ca + cb) * hv * d;
+        const double hv = P.h * vdr;
+        if (P.gamma_is_7) {
+            // with c = c0 (rho/rho0)^3, -alpha (c_a + c_b) / (rho_a + rho_b) equals
+            // kc64 (rho_a^2 - rho_a rho_b + rho_b^2) (a^3 + b^3 = (a + b)(a^2 - ab + b^2)),
+            // so Pi_ab = kc64 (...) mu_ab needs the one reciprocal of mu_ab only
+            mu = hv / (r2 + P.eta2);
+            if (vdr < 0.0) Pi = P.kc64 * fma(vb.w, vb.w - va.w, va.w * va.w) * mu;
+        } else {
+            // one reciprocal for both quotients: d = 1/((r^2 + eta^2)(rho_a + rho_b))
+            const double S = va.w + vb.w;
+            const double d = 1.0 / ((r2 + P.eta2) * S);
+            mu = hv * S * d;
+            if (vdr < 0.0) {
+                const double rb = vb.w * P.inv_rho0;
+                const double cb = P.c0 * pow(rb, 0.5 * (P.gamma - 1.0));
+                Pi = -P.alpha * (ca + cb) * hv * d;
+            }
         }
         if (P.tensile) Pi += tensile64(P, q, pa.w, pb.w);
         double coef = -(pa.w + pb.w + Pi) * F;
@@ -364,7 +374,9 @@ __device__ __forceinline__ void pi64_item(
 
 // One queue: the nfi fluid items, then the boundary items (as k_pi32).  The
 // particles outside the grid have no item; their outputs are zeroed here.
-__global__ void __launch_bounds__(W64_WARPS * 32)
+// Registers are held to 3 resident CTAs per SM (without the bound the compiler
+// takes 128 and spills).
+__global__ void __launch_bounds__(W64_WARPS * 32, 3)
 k_pi64w(DevParams P, int nf, int nb, const uint32_t *__restrict__ items_f,
         const uint32_t *__restrict__ items_b,
         const uint32_t *__restrict__ ctr, int use_b, uint32_t *__restrict__ next_p,
