@@ -118,9 +118,19 @@ __device__ __forceinline__ void pair_adj(const DevParams &P, double rx, double r
     double F, dFr;
     kernel_factor(P, r2, &F, &dFr);
     const double vdr = vx * rx + vy * ry + vz * rz;
-    const double den = r2 + P.eta2, S = A.rho + rho_b;
-    const double d = 1.0 / (den * S);
-    const double iden = d * S, iS = d * den;
+    const double den = r2 + P.eta2;
+    // K = -alpha (c_a + c_b) / (rho_a + rho_b); for gamma = 7 the polynomial
+    // kc64 (rho_a^2 - rho_a rho_b + rho_b^2) (pi.cu), so only 1/den is needed
+    double iden, iS = 0.0, t = 0.0;
+    if (P.gamma_is_7) {
+        iden = 1.0 / den;
+        t = fma(rho_b, rho_b - A.rho, A.rho * A.rho);
+    } else {
+        const double S = A.rho + rho_b;
+        const double d = 1.0 / (den * S);
+        iden = d * S;
+        iS = d * den;
+    }
     const double mu = P.h * vdr * iden;
     const double dGx = FLUID_B ? gFax - gFbx : gFax;
     const double dGy = FLUID_B ? gFay - gFby : gFay;
@@ -130,7 +140,7 @@ __device__ __forceinline__ void pair_adj(const DevParams &P, double rx, double r
     const double cs = A.c + c_b;
     double K = 0.0, Pi = 0.0;
     if (vdr < 0.0) {
-        K = -P.alpha * cs * iS;
+        K = P.gamma_is_7 ? P.kc64 * t : -P.alpha * cs * iS;
         Pi = K * mu;
     }
     const double Q = A.pr + pr_b + Pi;
@@ -150,8 +160,14 @@ __device__ __forceinline__ void pair_adj(const DevParams &P, double rx, double r
     l.vz += cvv * rz;
     double dPi = 0.0;
     if (vdr < 0.0) {
-        dPi = -P.alpha * mu * (A.dc * iS - cs * iS * iS);
-        l.alpha += mF * s1 * cs * mu * iS;   // (-m F s1) (-(c_a + c_b) mu / (rho_a + rho_b))
+        if (P.gamma_is_7) {
+            // dK/drho_a = kc64 (2 rho_a - rho_b); dPi/dalpha = -(c0/rho0^3) t mu
+            dPi = P.kc64 * fma(2.0, A.rho, -rho_b) * mu;
+            l.alpha += mF * s1 * P.kcu64 * t * mu;   // (-m F s1) dPi/dalpha
+        } else {
+            dPi = -P.alpha * mu * (A.dc * iS - cs * iS * iS);
+            l.alpha += mF * s1 * cs * mu * iS;   // (-m F s1) (-(c_a + c_b) mu / (rho_a + rho_b))
+        }
     }
     l.rho += Cc * (A.dpr + dPi);
 }
@@ -170,11 +186,18 @@ __device__ __forceinline__ double pair_adj_rho_b(const DevParams &P, double rx, 
     const double vdr = vx * rx + vy * ry + vz * rz;
     double dPi = 0.0;
     if (vdr < 0.0) {
-        const double den = r2 + P.eta2, S = rho_a + B.rho;
-        const double d = 1.0 / (den * S);
-        const double iS = d * den, mu = P.h * vdr * d * S;
-        const double cs = c_a + B.c;
-        dPi = -P.alpha * mu * (B.dc * iS - cs * iS * iS);
+        const double den = r2 + P.eta2;
+        if (P.gamma_is_7) {
+            // dK/drho_b = kc64 (2 rho_b - rho_a) (pair_adj)
+            const double mu = P.h * vdr / den;
+            dPi = P.kc64 * fma(2.0, B.rho, -rho_a) * mu;
+        } else {
+            const double S = rho_a + B.rho;
+            const double d = 1.0 / (den * S);
+            const double iS = d * den, mu = P.h * vdr * d * S;
+            const double cs = c_a + B.c;
+            dPi = -P.alpha * mu * (B.dc * iS - cs * iS * iS);
+        }
     }
     return Cc * (B.dpr + dPi);
 }

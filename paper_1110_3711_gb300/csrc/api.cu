@@ -94,7 +94,8 @@ DevParams derive(const sph_params &p, const int dims[3], uint32_t ncells)
     double aD = 1.0 / (M_PI * p.h * p.h * p.h);
     d.kA64 = aD / (p.h * p.h);
     d.kB64 = -0.75 * aD / p.h;
-    d.kc64 = -p.alpha * p.c0 / (p.rho0 * p.rho0 * p.rho0);
+    d.kcu64 = p.c0 / (p.rho0 * p.rho0 * p.rho0);
+    d.kc64 = -p.alpha * d.kcu64;
     d.cell_af = (float)(1.0 / p.cell_size);
     d.cell_eabsf = (float)fmax(0x1p-60, 0x1p-124 / p.cell_size);  // inf: always the float64 path
     for (int k = 0; k < 3; ++k) {

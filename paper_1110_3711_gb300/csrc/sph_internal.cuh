@@ -47,6 +47,7 @@ struct DevParams {
     double h, s, inv_s, rho0, inv_rho0, gamma, c0, alpha, eta2, cfl, mass, B, fixed_dt;
     double invh, kA64, kB64;  // 1/h and the grad-W factor constants (see pi.cu)
     double kc64;              // -alpha c0 / rho0^3 (viscosity factor for gamma = 7, see pi.cu)
+    double kcu64;             // c0 / rho0^3 (the same without -alpha, for d/d alpha in the adjoint)
     double g[3];
     double dom_min[3];
     int nx, ny, nz;
