@@ -59,6 +59,23 @@ def test_adjoint_matches_oracle_gradient(torch_mod):
     assert gag == pytest.approx(gao, rel=1e-8)
 
 
+def test_adjoint_general_gamma_matches_oracle(torch_mod):
+    """The adjoint with a Tait exponent other than 7 (general sound speed and
+    the c_bar / rho_bar form in the pair derivative, not the polynomial of
+    gamma = 7) against the gradient oracle."""
+    import copy
+    from oracle import grad as G
+    c, spos = _case()
+    p = copy.copy(c.params)
+    p.gamma = 5.0
+    c = type(c)(**{**c.__dict__, "params": p})
+    Jo, gvo, gao = G.gradient(c, c.vel[:c.n_f], 0.1, STEPS, DT, WINDOW, spos)
+    Jg, gvg, gag, _ = _gpu_grad(torch_mod, c, spos, k=7)
+    assert Jg == pytest.approx(Jo, rel=1e-12)
+    assert np.abs(gvg - gvo).max() <= 1e-8 * np.abs(gvo).max()
+    assert gag == pytest.approx(gao, rel=1e-8)
+
+
 def test_checkpoint_interval_does_not_change_gradient(torch_mod):
     c, spos = _case()
     ref = _gpu_grad(torch_mod, c, spos, k=1)

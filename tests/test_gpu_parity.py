@@ -177,6 +177,49 @@ def test_pi_fp64_matches_oracle(torch_mod, O, case_fn, pi_kernel):
     assert mx[1] == pytest.approx(max(O.sound(c.params, r) for r in rho), rel=1e-13)
 
 
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread"])
+@pytest.mark.parametrize("gamma,alpha", [(5.0, 0.1), (7.0, 0.0)])
+def test_pi_fp64_other_gamma_and_no_viscosity(torch_mod, O, pi_kernel, gamma, alpha):
+    """float64 PI with a Tait exponent other than 7 (the general sound speed
+    c0 (rho/rho0)^((gamma-1)/2) and the c_bar / rho_bar form of the viscosity,
+    not the polynomial of gamma = 7) and with the artificial viscosity switched
+    off, against the oracle."""
+    import copy
+    c = dam_break(0.02)
+    vel, rho = _random_state(c, 4)
+    p = copy.copy(c.params)
+    p.gamma, p.alpha = gamma, alpha
+    c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho, "params": p})
+    sim = make_sim(c2, "fp64", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(p, c.n_f, c.n_b, c.pos, vel, rho)
+    assert np.abs(ace - oace).max() <= 1e-12 * np.abs(oace).max()
+    assert np.abs(ar - oar).max() <= 1e-12 * np.abs(oar).max()
+    assert mx[2] == pytest.approx(ovm, rel=1e-13)
+
+
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "warp_sym"])
+def test_pi_fp32_split_no_viscosity(torch_mod, O, pi_kernel):
+    """float32 PI with the artificial viscosity switched off (alpha = 0: the
+    viscosity factor of the pair terms vanishes) against the oracle."""
+    import copy
+    c = dam_break(0.02)
+    vel, rho = _random_state(c, 5)
+    p = copy.copy(c.params)
+    p.alpha = 0.0
+    c2 = type(c)(**{**c.__dict__, "vel": vel, "rho": rho, "params": p})
+    sim = make_sim(c2, "fp32", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(p, c.n_f, c.n_b, c.pos, vel, rho)
+    assert np.abs(ace - oace).max() / (9.81 + np.abs(oace).max()) < 2e-5
+    assert np.abs(ar - oar).max() / np.abs(oar).max() < 2e-5
+    assert mx[2] == pytest.approx(ovm, rel=1e-5)
+
+
 @pytest.mark.parametrize("pi_kernel", ["warp", "thread", "thread_fastcells", "warp_sym"])
 def test_pi_fp32_split_matches_oracle(torch_mod, O, pi_kernel):
     """float32 PI on cell-relative offsets, every PI kernel design: errors

@@ -124,3 +124,31 @@ def test_front_objective_forward_and_gradient(oracle_lib, G):
         fd = (jp - jm) / (2 * eps)
         an = float((gv * d).sum())
         assert abs(fd - an) <= 1e-6 * abs(an)
+
+
+def test_gradient_general_gamma_matches_finite_differences(oracle_lib, G):
+    """Tait exponent 5 (the general sound speed c0 (rho/rho0)^2 and the
+    c_bar / rho_bar viscosity, not the gamma = 7 form): the gradient oracle's
+    forward equals the C oracle's and its gradient matches central differences
+    of the C oracle run with the same exponent."""
+    c = small_dam(0.02)
+    c.params = copy.copy(c.params)
+    c.params.gamma = 5.0
+    spos = wall_sensors(c, wall="back", n_y=2, n_z=2, z_top=0.12)
+    steps, window = 25, 8
+    v0 = c.vel[:c.n_f].copy()
+    J, gv, ga = G.gradient(c, v0, 0.1, steps, DT, window, spos)
+    assert J == pytest.approx(G.objective_c(c, v0, 0.1, steps, DT, window, spos), rel=1e-12)
+    rng = np.random.default_rng(5)
+    for _ in range(2):
+        d = rng.normal(size=v0.shape)
+        eps = 1e-7
+        jp = G.objective_c(c, v0 + eps * d, 0.1, steps, DT, window, spos)
+        jm = G.objective_c(c, v0 - eps * d, 0.1, steps, DT, window, spos)
+        fd = (jp - jm) / (2 * eps)
+        an = float((gv * d).sum())
+        assert abs(fd - an) <= 1e-6 * abs(an)
+    eps = 1e-6
+    fd_a = (G.objective_c(c, v0, 0.1 + eps, steps, DT, window, spos)
+            - G.objective_c(c, v0, 0.1 - eps, steps, DT, window, spos)) / (2 * eps)
+    assert fd_a == pytest.approx(ga, rel=1e-6)
