@@ -144,24 +144,29 @@ __device__ __forceinline__ void pi32_item(
             }
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
-            witems::lockstep_tests<true>(S.A, S.M, n, lane, F);
+            uint32_t cm = witems::lockstep_tests<true>(S.A, S.M, n, lane, F);
             // |x|^2 has served the tests: the pair walk reads P/rho^2 from its place
             __syncwarp();
             for (int q2 = 0; q2 < nch; ++q2) S.A[q2 * 32 + lane].w = S.Pr[q2 * 32 + lane];
             __syncwarp();
             // ---- every lane walks its own hits (about 112 per lane in all), in
-            // staging order: candidate k of chunk q is bit 31 - k of its mask
-            int q = 0;
-            uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
+            // staging order: candidate k of chunk q is bit 31 - k of its mask.
+            // cm has bit q set when chunk q holds a hit of this lane, so a lane
+            // that has finished a chunk moves to its next one in one step (no
+            // loop over empty chunks while the rest of the warp waits)
+            int qb = 0;
+            uint32_t m = 0u;
             for (;;) {
-                while (m == 0u && q + 1 < nch) {
-                    ++q;
+                if (m == 0u) {
+                    if (cm == 0u) break;
+                    const int q = __ffs(cm) - 1;
+                    cm &= cm - 1u;
                     m = S.M[q][lane];
+                    qb = q * 32;
                 }
-                if (m == 0u) break;
                 const int k = __clz(m);
                 m &= 0x7fffffffu >> k;
-                const int ls = q * 32 + k;
+                const int ls = qb + k;
                 const float4 b = S.A[ls];
                 pair_acc32<MOMENTUM, TENSILE>(P, F.x - b.x, F.y - b.y, F.z - b.z, pa.w, va, rho2a,
                                               S.V[ls], b.w, o);

@@ -251,11 +251,13 @@ __device__ __forceinline__ Box target_box(const Frame &F)
 // is set when candidate q * 32 + k is a hit of this lane's target.  The sign
 // of t - thr is shifted into two independent 16-candidate masks (candidate k
 // lands at bit 15 - k of its half), which are joined (and bit-reversed unless
-// MSB_FIRST).  A last chunk of at most 16 candidates tests one half.
+// MSB_FIRST).  A last chunk of at most 16 candidates tests one half.  Returns
+// the lane's non-empty chunks: bit q set when M[q][lane] != 0.
 template <bool MSB_FIRST>
-__device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32], int n,
-                                               int lane, const Frame &F)
+__device__ __forceinline__ uint32_t lockstep_tests(const float4 *A, uint32_t (*M)[32], int n,
+                                                   int lane, const Frame &F)
 {
+    uint32_t cm = 0u;
     const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
     const int nch = (n + 31) >> 5;
     for (int q = 0; q < nch; ++q) {
@@ -280,7 +282,9 @@ __device__ __forceinline__ void lockstep_tests(const float4 *A, uint32_t (*M)[32
         }
         const uint32_t w = (lo << 16) | hi;
         M[q][lane] = MSB_FIRST ? w : __brev(w);
+        cm |= (w != 0u ? 1u : 0u) << q;
     }
+    return cm;
 }
 
 // Step 2 for one set: sample slots k0, k0 + 1, ... of pass `pass` (np slots,
@@ -398,34 +402,6 @@ __device__ __forceinline__ void stage_and_test(const DevParams &P, Smem &S, int 
             __syncwarp();
         }
     }
-}
-
-// Steps 1-4 above; hit(j, blist) runs for every hit of this lane (blist:
-// candidate j of the boundary list).  Every lane of the warp must call it.
-template <bool FLUID_TARGETS, class Hit>
-__device__ __forceinline__ void for_each_hit(const DevParams &P, Smem &S, int lane, const Item &I,
-                                             const Frame &F, const int32_t *__restrict__ fstart,
-                                             const float4 *__restrict__ fposf,
-                                             const int32_t *__restrict__ bstart,
-                                             const float4 *__restrict__ bposf,
-                                             const uint32_t *__restrict__ fcell, Hit &&hit)
-{
-    stage_and_test<FLUID_TARGETS>(P, S, lane, I, F, fstart, fposf, bstart, bposf, fcell,
-                                  [&](int nch) {
-        int q = 0;
-        uint32_t m = nch > 0 ? S.M[0][lane] : 0u;
-        for (;;) {
-            while (m == 0u && q + 1 < nch) {
-                ++q;
-                m = S.M[q][lane];
-            }
-            if (m == 0u) break;
-            const int ls = q * 32 + __ffs(m) - 1;
-            m &= m - 1u;
-            const uint32_t jj = S.J[ls];
-            hit((int)(jj & 0x7fffffffu), FLUID_TARGETS && (jj >> 31) != 0u);
-        }
-    });
 }
 
 // Steps 1-3 above, then a balanced walk: the hits of a tested set, taken in
