@@ -24,6 +24,11 @@
 //      stay balanced) and evaluates the pair terms of the oracle (cubic-spline
 //      gradient, Tait pressure, artificial viscosity, continuity) from the
 //      staged data, recomputing r_ab exactly from the shifted offsets.
+// An item of at most 16 targets (a thinly filled cell, the free surface)
+// would leave half the lanes idle through the walk: there each target has two
+// lanes, l and l + 16, and at most 8 targets four lanes, l + 8 j; the lanes of
+// a target take the candidates k = j mod 2 (or mod 4) of every chunk, and
+// their sums are joined in a fixed order by shuffles at the end.
 // Work items are taken from a list built by NL with an atomic counter, so the
 // grid is persistent (one resident set of CTAs) and balances itself.  Fluid
 // items hold the particles of one cell (about 27 at rest; a fuller cell gives
@@ -33,9 +38,9 @@
 // neighbourhoods (x-runs from the first cell - 1 to the last + 1); each
 // candidate is shifted by its own cell's x distance from the first cell, each
 // target by its cell's.  Fluid and boundary items form one queue (fluid first)
-// served by one launch.  Sums of a target are accumulated by one lane in
-// candidate order, so results do not depend on the order the items are
-// processed in.
+// served by one launch.  Sums of a target are accumulated in candidate order
+// by one lane (or by each of its lanes, then joined), so results do not depend
+// on the order the items are processed in.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -93,7 +98,18 @@ __device__ __forceinline__ void pi32_item(
     double &f2max, float &vismax, bool &bad)
 {
     // ---- the item: targets [i0, i0 + nt) of cells c .. c + (cx1 - cx) of one x row
-    const witems::Item I = witems::item_of(P, items, it, tcell, lane);
+    witems::Item I = witems::item_of(P, items, it, tcell, lane);
+    // g lanes per target: 2 for at most 16 targets, 4 for at most 8; target
+    // t has lanes t + (32 / g) j, j < g, and lane j of a target keeps the hits
+    // at chunk bits b = j mod g
+    const int g = I.nt <= 8 ? 4 : (I.nt <= 16 ? 2 : 1);
+    if (g > 1) {
+        const int tl = lane & (32 / g - 1);
+        I.active = tl < I.nt;
+        I.i = I.i0 + (I.active ? tl : 0);
+    }
+    const uint32_t keep = g == 1 ? 0xffffffffu
+                        : (g == 2 ? 0x55555555u << (lane >> 4) : 0x11111111u << (lane >> 3));
     const int i = I.i;
     const float4 pa = tposp[i], va = tvelr[i];
     // the target in the item's frame, units of h; the lockstep test decides
@@ -144,7 +160,7 @@ __device__ __forceinline__ void pi32_item(
             }
             __syncwarp();
             // ---- lockstep distance tests, one hit bit per candidate
-            uint32_t cm = witems::lockstep_tests<true>(S.A, S.M, n, lane, F);
+            uint32_t cm = witems::lockstep_tests<true>(S.A, S.M, n, lane, F, keep);
             // |x|^2 has served the tests: the pair walk reads P/rho^2 from its place
             __syncwarp();
             for (int q2 = 0; q2 < nch; ++q2) S.A[q2 * 32 + lane].w = S.Pr[q2 * 32 + lane];
@@ -175,7 +191,18 @@ __device__ __forceinline__ void pi32_item(
         }
     }
 
-    if (I.active) {
+    if (g > 1) {
+        // lane t collects the sums of lanes t + 16 (and t + 8, t + 24): a fixed
+        // tree over the lanes of target t
+        for (int d = 16; d >= 32 / g; d >>= 1) {
+            o.ax += __shfl_down_sync(0xffffffffu, o.ax, d);
+            o.ay += __shfl_down_sync(0xffffffffu, o.ay, d);
+            o.az += __shfl_down_sync(0xffffffffu, o.az, d);
+            o.ar += __shfl_down_sync(0xffffffffu, o.ar, d);
+            o.vis = fmaxf(o.vis, __shfl_down_sync(0xffffffffu, o.vis, d));
+        }
+    }
+    if (I.active && lane < 32 / g) {
         if (MOMENTUM) {
             const float ax = fmaf(P.nmkBf, o.ax, P.gf[0]);
             const float ay = fmaf(P.nmkBf, o.ay, P.gf[1]);

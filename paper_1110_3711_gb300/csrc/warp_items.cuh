@@ -251,11 +251,14 @@ __device__ __forceinline__ Box target_box(const Frame &F)
 // is set when candidate q * 32 + k is a hit of this lane's target.  The sign
 // of t - thr is shifted into two independent 16-candidate masks (candidate k
 // lands at bit 15 - k of its half), which are joined (and bit-reversed unless
-// MSB_FIRST).  A last chunk of at most 16 candidates tests one half.  Returns
-// the lane's non-empty chunks: bit q set when M[q][lane] != 0.
+// MSB_FIRST).  A last chunk of at most 16 candidates tests one half.  Only
+// the bits set in keep are kept (a lane that shares its target with other
+// lanes takes a share of the candidates).  Returns the lane's non-empty
+// chunks: bit q set when M[q][lane] != 0.
 template <bool MSB_FIRST>
 __device__ __forceinline__ uint32_t lockstep_tests(const float4 *A, uint32_t (*M)[32], int n,
-                                                   int lane, const Frame &F)
+                                                   int lane, const Frame &F,
+                                                   uint32_t keep = 0xffffffffu)
 {
     uint32_t cm = 0u;
     const float m2x = -2.0f * F.x, m2y = -2.0f * F.y, m2z = -2.0f * F.z;
@@ -280,7 +283,7 @@ __device__ __forceinline__ uint32_t lockstep_tests(const float4 *A, uint32_t (*M
                 lo = __funnelshift_l(__float_as_uint(ta), lo, 1);
             }
         }
-        const uint32_t w = (lo << 16) | hi;
+        const uint32_t w = ((lo << 16) | hi) & keep;
         M[q][lane] = MSB_FIRST ? w : __brev(w);
         cm |= (w != 0u ? 1u : 0u) << q;
     }

@@ -256,6 +256,25 @@ def test_pi_fp32_dense_cells(torch_mod, O, pi_kernel):
     assert mx[2] == pytest.approx(ovm, rel=1e-5)
 
 
+@pytest.mark.parametrize("pi_kernel", ["warp", "thread", "warp_sym"])
+def test_pi_fp32_sparse_cells(torch_mod, O, pi_kernel):
+    """Cells of 1 to 17 particles (random cloud, about 8 per occupied cell):
+    fluid items of at most 8 and of 9 to 16 targets, where the warp kernel
+    gives each target four or two lanes that share its candidates."""
+    c = random_cloud(3000, box=0.2, dp=0.01, n_b=500, seed=33)
+    cnt = np.bincount(O.cells(c.params, c.pos[:c.n_f]))
+    cnt = cnt[cnt > 0]
+    assert (cnt <= 8).any() and ((cnt > 8) & (cnt <= 16)).any() and (cnt > 16).any()
+    sim = make_sim(c, "fp32", pi_kernel=pi_kernel)
+    sim.neighbour_list()
+    sim.interact()
+    ace, ar, mx = sim.forces()
+    oace, oar, ovm, _, _ = O.interact(c.params, c.n_f, c.n_b, c.pos, c.vel, c.rho)
+    assert np.abs(ace - oace).max() / (9.81 + np.abs(oace).max()) < 2e-5
+    assert np.abs(ar - oar).max() / np.abs(oar).max() < 2e-5
+    assert mx[2] == pytest.approx(ovm, rel=1e-5)
+
+
 @pytest.mark.parametrize("pi_kernel", ["warp", "warp_sym"])
 def test_pi_fp32_with_particles_outside_the_grid(torch_mod, O, pi_kernel):
     """Fluid particles outside the cell grid take no part in PI (sentinel cell);
