@@ -364,6 +364,27 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def cpu_model():
+    """The host CPU as /proc/cpuinfo names it (x86: model name; Arm: the
+    implementer and part numbers), else what platform reports."""
+    fields = {}
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k, _, v = ln.partition(":")
+                k, v = k.strip(), v.strip()
+                if k and v and k not in fields:
+                    fields[k] = v
+    except OSError:
+        pass
+    if "model name" in fields:
+        return fields["model name"]
+    if "CPU part" in fields:
+        return f"Arm implementer {fields.get('CPU implementer', '?')} part {fields['CPU part']}"
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def oracle_step_seconds(O, case, stride, cores):
     """Time one oracle step on the host: list build and PI on every stride-th
     target (scaled by stride), the time step and SU on all particles."""
@@ -396,7 +417,8 @@ def cpu_baseline(case, budget_s=15.0):
         if el > budget_s or n >= 50:
             break
     pairs = st.last_counts[1] + st.last_counts[3]
-    return {"value": n / el, "unit": "steps/s", "cores": cores, "kind": "oracle",
+    return {"value": n / el, "unit": "steps/s", "cores": cores, "cpu_model": cpu_model(),
+            "kind": "oracle",
             "sample": f"{n} full oracle steps (NL+PI+SU, all {case.n} particles, FP64) "
                       f"from the initial state, {el:.1f} s wall",
             "interactions_per_s": float(pairs) * n / el}
@@ -433,7 +455,7 @@ def run_reference(args, workload):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_block(workload, case),
             "cpu_baseline": {"value": value, "unit": "steps/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "cpu_model": cpu_model(), "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
