@@ -51,7 +51,8 @@
 
 // Staged candidates per warp and set.  224 (36.8 KB of shared memory per CTA
 // of 4 warps) admits 6 CTAs, 24 warps, per SM; 256 admitted 5 (PI 2.7 %
-// slower at 1M on GB300).
+// slower at 1M on GB300), and 160 with 7 or 8 CTAs (72 or 64 registers) was
+// 7 % slower: fuller sets count for more than more resident warps.
 #ifndef SPH_PI_CAP
 #define SPH_PI_CAP 224
 #endif
